@@ -1,0 +1,171 @@
+/*
+ * fp.h -- C ABI of the GB300 batched Neel-rotation Fokker-Planck library (libfp.so).
+ *
+ * The library computes, for many independent instances, the mean magnetic
+ * moment of an ensemble of immobilised, uniaxially anisotropic nanoparticles
+ * under an MPI drive field, and the normalised induced-voltage signal:
+ *
+ *   Eq. mean_magmom_FP (Sec. 2.1):  m_bar(t) = m0 * integral_{S^2} m f(m, t) dm
+ *   Eq. FP-general     (Sec. 2.1):  df/dt = div(1/(2 tau) grad f) - div(b f)
+ *   Eq. convection     (Sec. 2.1):  b = p1 H x m + p2 (m x H) x m
+ *                                       + p3 (n.m) n x m + p4 (n.m) (m x n) x m
+ *   Neel constants     (Sec. 2.1):  p1 = g mu0, p2 = g alpha mu0, p3 = 2 g K/Ms,
+ *                                   p4 = alpha p3, tau = V Ms / (2 kB T g alpha),
+ *                                   g = gamma / (1 + alpha^2), V = pi d^3 / 6
+ *   Applied field      (Sec. 2):    H(r, t) = H_SF(r) + H_DF(t); the PDE has no
+ *                                   r-derivative, so each voxel offset is an
+ *                                   independent instance (Sec. 2.1, last paragraph)
+ *   Signal             (Sec. 2.2):  phi_hat_k = 1/(m0 T) int_0^T p . dm_bar/dt
+ *                                   exp(-2 pi i t k / T) dt   (model M1)
+ *
+ * Units: SI, with every magnetic field given as B = mu0 H in tesla (the paper
+ * writes fields in T/mu0), so mu0 never enters.  Angles in radians; the easy
+ * axis is n = (sin theta cos phi, sin theta sin phi, cos theta); the paper's
+ * in-plane angle vartheta (Sec. 2.2 (iii)) is theta = pi/2, phi = vartheta.
+ *
+ * Discretisation: real spherical-harmonic Galerkin expansion of f truncated at
+ * degree L (N = (L+1)^2 coefficients), the operator applied matrix-free from
+ * closed-form coupling coefficients in the easy-axis frame.  Time integration:
+ * 3-stage Radau IIA (order 5, L-stable) with per-instance adaptive steps,
+ * simplified Newton iterations whose residuals are FP64 and whose iteration
+ * matrices are factorised in FP32.  Initial state: Boltzmann equilibrium at
+ * H(0) including the anisotropy.
+ *
+ * Conventions for every entry point:
+ *   - return 0 on success, a negative FP_E* code on argument or CUDA error;
+ *     fp_last_error() then holds a one-line message (thread-local);
+ *   - "d_" pointers are DEVICE pointers owned by the caller; "h_" pointers are
+ *     host pointers owned by the caller; the library keeps none of them;
+ *   - calls with a stream argument are asynchronous on that stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream);
+ *   - the context owns only its coefficient tables and constants (allocated
+ *     once in fp_setup) and is not thread-safe: one host thread per context.
+ */
+#ifndef FP_H_
+#define FP_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (return values) ---------------------------------------- */
+#define FP_OK            0
+#define FP_EINVAL       -1   /* bad argument (NULL, size, range)               */
+#define FP_ECUDA        -2   /* a CUDA runtime call failed                     */
+#define FP_ENOMEM       -3   /* host or device allocation failed (fp_setup)    */
+#define FP_EUNSUPPORTED -4   /* valid request outside what this build supports */
+
+/* ---- per-instance status codes (d_status) ------------------------------- */
+#define FP_STATUS_OK             0
+#define FP_STATUS_MAXSTEPS       1  /* step budget (fp_tol.max_steps) exhausted */
+#define FP_STATUS_STEP_UNDERFLOW 2  /* step size fell below 1e-6 of the sample spacing */
+#define FP_STATUS_NONFINITE      3  /* NaN/Inf in the state                      */
+#define FP_STATUS_NEWTON_FAIL    4  /* Newton iteration failed at the minimum step */
+#define FP_STATUS_BAD_INPUT      5  /* instance parameters out of range (L, K, d) */
+
+/* Material of Sec. 2.1 / 2.4.1: saturation magnetisation Ms [A/m], Gilbert
+ * damping alpha, gyromagnetic ratio gamma [rad/(s T)], temperature T_B [K]. */
+typedef struct {
+    double Ms, alpha, gamma, T_B;
+} fp_material;
+
+/* Drive field H_DF of Sec. 2 / Sec. 2.4, per lab axis k:
+ *     B_k(t) = amp[k] * sin(2 pi freq[k] t + phase[k])     [T]
+ * A cosine Lissajous drive has phase pi/2.  One period lasts `period` seconds
+ * and is sampled at samples_per_period equidistant times; the output holds
+ * output_periods periods after warmup_periods periods:
+ *     t_j = (warmup_periods + j / samples_per_period) * period,
+ *     j = 0 .. output_periods * samples_per_period - 1.                      */
+typedef struct {
+    double amp[3];
+    double freq[3];
+    double phase[3];
+    double period;
+    int samples_per_period;
+    int warmup_periods;
+    int output_periods;
+    int pad_;
+} fp_drive;
+
+/* Integrator controls.  Local error per step (max norm) must stay below
+ * atol + rtol * max|c|.  max_steps bounds accepted+rejected steps per
+ * instance; newton_max_iter bounds Newton iterations per step;
+ * refactor_every bounds how many steps reuse one FP32 factorisation. */
+typedef struct {
+    double rtol, atol;
+    int max_steps;
+    int newton_max_iter;
+    int refactor_every;
+    int checkpoint_every;   /* adjoint checkpoint stride in steps (fp_grad) */
+} fp_tol;
+
+/* One instance (Sec. 2.2 (iii) model m_bar_(D, K, vartheta) at one voxel):
+ * offset field h_off = mu0 H_SF(r) [T] in the lab frame, easy axis (theta,
+ * phi), anisotropy K [J/m^3], core diameter d [m], truncation degree L
+ * (2 <= L <= fp_max_degree()).  64 bytes, 8-byte aligned.                 */
+typedef struct {
+    double h_off[3];
+    double theta, phi;
+    double K, d;
+    int L;
+    int flags;              /* reserved, must be 0 */
+} fp_instance;
+
+typedef struct fp_ctx fp_ctx;
+
+/* Largest truncation degree this build supports. */
+int fp_max_degree(void);
+
+/* Create a context: copies the material, drive and tolerances, builds the
+ * closed-form coupling tables for degrees <= L_max on the current CUDA device.
+ * Allocates device memory here and only here.  *out receives the context. */
+int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol,
+             int L_max, fp_ctx** out);
+
+/* Release a context and its device tables.  NULL is accepted. */
+int fp_destroy(fp_ctx* ctx);
+
+/* Number of output samples per instance: output_periods * samples_per_period. */
+int fp_num_samples(const fp_ctx* ctx);
+
+/* Solve n instances (Sec. 2.1, Eq. FP-general with the readout of
+ * Eq. mean_magmom_FP divided by m0).  Layouts (row-major, FP64):
+ *   d_inst  [n]            fp_instance, device memory
+ *   d_m     [n][S][3]      <m>(t_j) in the lab frame (may be NULL)
+ *   d_dmdt  [n][S][3]      d<m>/dt(t_j), exact (l = 1 rows of A(t_j) c) (may be NULL)
+ *   d_status[n]            FP_STATUS_* per instance
+ *   d_stats [n][4] or NULL accepted steps, rejected steps, Newton iterations,
+ *                          factorisations
+ * with S = fp_num_samples(ctx).  n == 0 is a no-op.  Instances with a bad L
+ * or non-positive K < 0, d <= 0 get FP_STATUS_BAD_INPUT and zero outputs. */
+int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n,
+                   double* d_m, double* d_dmdt, int* d_status, int* d_stats,
+                   void* stream);
+
+/* Normalised signal of Sec. 2.2 (model M1 phi_hat, per unit m0) by the
+ * rectangle rule over the LAST output period of d_dmdt:
+ *   phi_hat[i][c][k] = (1/S_p) sum_{j<S_p} (p_c . dmdt[i][j0 + j]) e^{-2 pi i j k / S_p}
+ * with S_p = samples_per_period, j0 = S - S_p, channel directions p_c
+ * (h_channels [C][3], host memory, homogeneous receive coils, Sec. 2.2 (ii)),
+ * k = 0..k_max (k_max < S_p).  Output d_phihat [n][C][k_max+1][2] (re, im), FP64. */
+int fp_signal(fp_ctx* ctx, const double* d_dmdt, int n, int k_max,
+              const double* h_channels, int C, double* d_phihat, void* stream);
+
+/* Diagnostic (host only, no GPU needed): dense Galerkin matrix A of
+ * dc/dt = A c (Eq. FP-general tested against the real SH basis) for one
+ * instance in the EASY-AXIS frame (n = z), with the field B_nframe [T] already
+ * rotated into that frame, built from the same closed-form coupling tables
+ * the kernels use.  h_inst->L in [2, 64]; theta/phi are ignored.  h_A
+ * receives N*N doubles row-major, A[target][source], N = (L+1)^2, index
+ * i = l*l + l + m (real SH without Condon-Shortley phase). */
+int fp_operator_dense(const fp_material* mat, const fp_instance* h_inst,
+                      const double B_nframe[3], double* h_A);
+
+/* Text for a status or error code, and the last error message. */
+const char* fp_status_str(int code);
+const char* fp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FP_H_ */

@@ -1,0 +1,79 @@
+"""ctypes view of libfp.so (include/fp.h).  Argument marshalling only.
+
+The library is loaded from this package directory; a missing or unloadable
+library raises immediately -- there is no fallback implementation.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfp.so")
+
+FP_OK, FP_EINVAL, FP_ECUDA, FP_ENOMEM, FP_EUNSUPPORTED = 0, -1, -2, -3, -4
+STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT"}
+
+EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_solve_batch",
+            "fp_signal", "fp_operator_dense", "fp_status_str", "fp_last_error"]
+
+
+class fp_material(C.Structure):
+    _fields_ = [("Ms", C.c_double), ("alpha", C.c_double), ("gamma", C.c_double), ("T_B", C.c_double)]
+
+
+class fp_drive(C.Structure):
+    _fields_ = [("amp", C.c_double * 3), ("freq", C.c_double * 3), ("phase", C.c_double * 3),
+                ("period", C.c_double), ("samples_per_period", C.c_int), ("warmup_periods", C.c_int),
+                ("output_periods", C.c_int), ("pad_", C.c_int)]
+
+
+class fp_tol(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_steps", C.c_int),
+                ("newton_max_iter", C.c_int), ("refactor_every", C.c_int), ("checkpoint_every", C.c_int)]
+
+
+class fp_instance(C.Structure):
+    _fields_ = [("h_off", C.c_double * 3), ("theta", C.c_double), ("phi", C.c_double),
+                ("K", C.c_double), ("d", C.c_double), ("L", C.c_int), ("flags", C.c_int)]
+
+
+assert C.sizeof(fp_instance) == 64
+assert C.sizeof(fp_drive) == 96
+
+_lib = None
+
+
+def lib():
+    """Load libfp.so once; raise if it is missing (build it with build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfp.so not built: run `python paper_2106_08040_gb300/build.py` "
+                           "(or __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.fp_max_degree.restype = i
+    L.fp_setup.argtypes = [C.POINTER(fp_material), C.POINTER(fp_drive), C.POINTER(fp_tol), i, C.POINTER(vp)]
+    L.fp_setup.restype = i
+    L.fp_destroy.argtypes = [vp]
+    L.fp_destroy.restype = i
+    L.fp_num_samples.argtypes = [vp]
+    L.fp_num_samples.restype = i
+    L.fp_solve_batch.argtypes = [vp, vp, i, vp, vp, vp, vp, vp]
+    L.fp_solve_batch.restype = i
+    L.fp_signal.argtypes = [vp, vp, i, i, C.POINTER(d), i, vp, vp]
+    L.fp_signal.restype = i
+    L.fp_operator_dense.argtypes = [C.POINTER(fp_material), C.POINTER(fp_instance), C.POINTER(d), C.POINTER(d)]
+    L.fp_operator_dense.restype = i
+    L.fp_status_str.argtypes = [i]
+    L.fp_status_str.restype = C.c_char_p
+    L.fp_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def check(rc, what):
+    if rc != FP_OK:
+        msg = lib().fp_last_error().decode(errors="replace")
+        raise RuntimeError("%s failed (%d): %s" % (what, rc, msg))
+    return rc

@@ -1,0 +1,254 @@
+// C ABI of libfp.so: context management, argument checks, launches, the
+// phi_hat kernel (Sec. 2.2, model M1 signal) and the host-side diagnostic
+// operator export.  See include/fp.h for the contract of every entry point.
+#include <cuda_runtime.h>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <vector>
+#include "fp_internal.h"
+
+struct DevTab {
+    const double* coef;
+    const int* src;
+    const int* tslot;
+    const double* lam;
+    const double* wdiag;
+};
+
+size_t fp_solver_smem_bytes(int L);
+int fp_launch_solve(const DevTab* tab, const fp_material* mat, const fp_drive* drv, const fp_tol* tol,
+                    const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
+                    int* d_status, int* d_stats, int grid, cudaStream_t st);
+int fp_upload_constants(const FpRadau* r, const double* glx, const double* glw);
+
+struct fp_ctx {
+    fp_material mat;
+    fp_drive drv;
+    fp_tol tol;
+    int L_max;
+    int device;
+    int num_sms;
+    FpTablesHost host;        // kept for fp_operator_dense
+    double* d_coef;
+    int* d_src;
+    int* d_tslot;
+    double* d_lam;
+    double* d_wdiag;
+    double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
+};
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(FP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));            \
+    } while (0)
+
+extern "C" {
+
+const char* fp_last_error(void) { return g_err; }
+
+const char* fp_status_str(int code) {
+    switch (code) {
+        case FP_OK: return "ok";
+        case FP_EINVAL: return "invalid argument";
+        case FP_ECUDA: return "CUDA error";
+        case FP_ENOMEM: return "out of memory";
+        case FP_EUNSUPPORTED: return "unsupported";
+        case FP_STATUS_MAXSTEPS: return "step budget exhausted";
+        case FP_STATUS_STEP_UNDERFLOW: return "step size underflow";
+        case FP_STATUS_NONFINITE: return "non-finite state";
+        case FP_STATUS_NEWTON_FAIL: return "Newton iteration failed";
+        case FP_STATUS_BAD_INPUT: return "bad instance parameters";
+        default: return "unknown code";
+    }
+}
+
+int fp_max_degree(void) { return FP_L_MAX; }
+
+int fp_destroy(fp_ctx* ctx) {
+    if (!ctx) return FP_OK;
+    cudaFree(ctx->d_coef);
+    cudaFree(ctx->d_src);
+    cudaFree(ctx->d_tslot);
+    cudaFree(ctx->d_lam);
+    cudaFree(ctx->d_wdiag);
+    cudaFree(ctx->d_tw);
+    fp_free_tables(&ctx->host);
+    delete ctx;
+    return FP_OK;
+}
+
+int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, int L_max, fp_ctx** out) {
+    if (!mat || !drive || !tol || !out) return fail(FP_EINVAL, "fp_setup: NULL argument");
+    *out = nullptr;
+    if (L_max < 2 || L_max > FP_L_MAX)
+        return fail(FP_EUNSUPPORTED, "fp_setup: L_max=%d outside [2, %d]", L_max, FP_L_MAX);
+    if (!(mat->Ms > 0 && mat->alpha > 0 && mat->gamma > 0 && mat->T_B > 0))
+        return fail(FP_EINVAL, "fp_setup: material constants must be positive");
+    if (!(drive->period > 0) || drive->samples_per_period < 2 || drive->warmup_periods < 0 ||
+        drive->output_periods < 1)
+        return fail(FP_EINVAL, "fp_setup: bad drive schedule");
+    if (!(tol->rtol > 0) || !(tol->atol >= 0) || tol->max_steps < 1 || tol->newton_max_iter < 1 ||
+        tol->refactor_every < 1)
+        return fail(FP_EINVAL, "fp_setup: bad tolerances");
+    fp_ctx* c = new (std::nothrow) fp_ctx();
+    if (!c) return fail(FP_ENOMEM, "fp_setup: host allocation");
+    c->mat = *mat;
+    c->drv = *drive;
+    c->tol = *tol;
+    c->L_max = L_max;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return fail(FP_ECUDA, "fp_setup: no CUDA device"); }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (fp_build_tables(L_max, &c->host) != FP_OK) { delete c; return fail(FP_ENOMEM, "fp_setup: tables"); }
+    const size_t N = (size_t)c->host.N;
+    int rc = FP_OK;
+    auto up = [&](void** dst, const void* src, size_t bytes) {
+        if (rc != FP_OK) return;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) { rc = fail(FP_ENOMEM, "fp_setup: cudaMalloc"); return; }
+        if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = fail(FP_ECUDA, "fp_setup: cudaMemcpy");
+    };
+    up((void**)&c->d_coef, c->host.coef, N * FP_NSLOT * sizeof(double));
+    up((void**)&c->d_src, c->host.src, N * FP_NSLOT * sizeof(int));
+    up((void**)&c->d_tslot, c->host.tslot, N * FP_NSLOT * sizeof(int));
+    up((void**)&c->d_lam, c->host.lam, N * sizeof(double));
+    up((void**)&c->d_wdiag, c->host.wdiag, N * sizeof(double));
+    std::vector<double> tw(2 * (size_t)drive->samples_per_period);
+    const double twopi = 6.283185307179586476925286766559;
+    for (int q = 0; q < drive->samples_per_period; ++q) {
+        double ang = twopi * (double)q / (double)drive->samples_per_period;
+        tw[2 * q] = std::cos(ang);
+        tw[2 * q + 1] = std::sin(ang);
+    }
+    up((void**)&c->d_tw, tw.data(), tw.size() * sizeof(double));
+    if (rc != FP_OK) { fp_destroy(c); return rc; }
+    FpRadau r;
+    fp_build_radau(&r);
+    double glx[FP_NGL], glw[FP_NGL];
+    fp_gauss_legendre(FP_NGL, glx, glw);
+    if (fp_upload_constants(&r, glx, glw) != FP_OK) { fp_destroy(c); return fail(FP_ECUDA, "fp_setup: constants"); }
+    *out = c;
+    return FP_OK;
+}
+
+int fp_num_samples(const fp_ctx* ctx) {
+    if (!ctx) return fail(FP_EINVAL, "fp_num_samples: NULL ctx");
+    return ctx->drv.output_periods * ctx->drv.samples_per_period;
+}
+
+int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, double* d_dmdt, int* d_status,
+                   int* d_stats, void* stream) {
+    if (!ctx) return fail(FP_EINVAL, "fp_solve_batch: NULL ctx");
+    if (n < 0) return fail(FP_EINVAL, "fp_solve_batch: n < 0");
+    if (n == 0) return FP_OK;
+    if (!d_inst || !d_status) return fail(FP_EINVAL, "fp_solve_batch: NULL instance or status buffer");
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_tslot, ctx->d_lam, ctx->d_wdiag};
+    size_t sm = fp_solver_smem_bytes(ctx->L_max);
+    int max_sm = 0;
+    cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if ((int)sm > max_sm)
+        return fail(FP_EUNSUPPORTED, "fp_solve_batch: %zu bytes of shared memory needed, %d available", sm, max_sm);
+    int grid = n < ctx->num_sms ? n : ctx->num_sms;
+    int rc = fp_launch_solve(&tab, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max, d_m, d_dmdt, d_status,
+                             d_stats, grid, (cudaStream_t)stream);
+    if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return FP_OK;
+}
+
+}  // extern "C"
+
+// phi_hat[i][c][k] = (1/S) sum_j (p_c . dmdt[i][j0 + j]) (cos - i sin)(2 pi j k / S)
+__global__ void fp_signal_kernel(const double* __restrict__ dmdt, int S_out, int S, int k_max,
+                                 const double* __restrict__ tw, int C, double3 ch0, double3 ch1, double3 ch2,
+                                 double3 ch3, double* __restrict__ out) {
+    extern __shared__ double su[];           // [C][S] projected samples
+    const int inst = blockIdx.x;
+    const double* d = dmdt + ((size_t)inst * S_out + (S_out - S)) * 3;
+    double3 chs[4] = {ch0, ch1, ch2, ch3};
+    for (int e = threadIdx.x; e < S * C; e += blockDim.x) {
+        int c = e / S, j = e - c * S;
+        const double* v = d + (size_t)j * 3;
+        su[e] = chs[c].x * v[0] + chs[c].y * v[1] + chs[c].z * v[2];
+    }
+    __syncthreads();
+    const int K = k_max + 1;
+    for (int e = threadIdx.x; e < C * K; e += blockDim.x) {
+        int c = e / K, k = e - c * K;
+        const double* u = su + (size_t)c * S;
+        double re = 0.0, im = 0.0;
+        int q = 0;
+        for (int j = 0; j < S; ++j) {
+            double uj = u[j];
+            re = fma(uj, __ldg(tw + 2 * q), re);
+            im = fma(-uj, __ldg(tw + 2 * q + 1), im);
+            q += k;
+            if (q >= S) q -= S;
+        }
+        double* o = out + (((size_t)inst * C + c) * K + k) * 2;
+        o[0] = re / S;
+        o[1] = im / S;
+    }
+}
+
+extern "C" int fp_signal(fp_ctx* ctx, const double* d_dmdt, int n, int k_max, const double* h_channels, int C,
+                         double* d_phihat, void* stream) {
+    if (!ctx) return fail(FP_EINVAL, "fp_signal: NULL ctx");
+    if (n < 0) return fail(FP_EINVAL, "fp_signal: n < 0");
+    if (n == 0) return FP_OK;
+    const int S = ctx->drv.samples_per_period, S_out = fp_num_samples(ctx);
+    if (!d_dmdt || !d_phihat || !h_channels) return fail(FP_EINVAL, "fp_signal: NULL buffer");
+    if (k_max < 0 || k_max >= S) return fail(FP_EINVAL, "fp_signal: k_max=%d outside [0, %d)", k_max, S);
+    if (C < 1 || C > 4) return fail(FP_EINVAL, "fp_signal: C=%d outside [1, 4]", C);
+    double3 ch[4];
+    for (int c = 0; c < 4; ++c)
+        ch[c] = c < C ? make_double3(h_channels[3 * c], h_channels[3 * c + 1], h_channels[3 * c + 2])
+                      : make_double3(0, 0, 0);
+    size_t sm = (size_t)S * C * sizeof(double);
+    if (sm > 200 * 1024) return fail(FP_EUNSUPPORTED, "fp_signal: period too long for shared memory");
+    if (cudaFuncSetAttribute(fp_signal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return fail(FP_ECUDA, "fp_signal: smem attribute");
+    fp_signal_kernel<<<n, 256, sm, (cudaStream_t)stream>>>(d_dmdt, S_out, S, k_max, ctx->d_tw, C, ch[0], ch[1],
+                                                          ch[2], ch[3], d_phihat);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FP_ECUDA, "fp_signal: launch: %s", cudaGetErrorString(e));
+    return FP_OK;
+}
+
+extern "C" int fp_operator_dense(const fp_material* mat, const fp_instance* h_inst, const double B_nframe[3],
+                                 double* h_A) {
+    if (!mat || !h_inst || !B_nframe || !h_A) return fail(FP_EINVAL, "fp_operator_dense: NULL argument");
+    const int L = h_inst->L;
+    if (L < 2 || L > 64) return fail(FP_EINVAL, "fp_operator_dense: L=%d outside [2, 64]", L);
+    FpTablesHost tb;
+    if (fp_build_tables(L, &tb) != FP_OK) return fail(FP_ENOMEM, "fp_operator_dense: tables");
+    const int N = tb.N;
+    FpParams P = fp_derive(*mat, h_inst->K, h_inst->d);
+    double s[8] = {-0.5 * P.p4, -P.p3, -P.p1 * B_nframe[2], -P.p1 * B_nframe[0], -P.p1 * B_nframe[1],
+                   -P.p2 * B_nframe[2], -P.p2 * B_nframe[0], -P.p2 * B_nframe[1]};
+    static const int grp[FP_NSLOT] = {0, 0, 1, 1, 2, 3, 3, 4, 4, 5, 5, 6, 6, 6, 6, 7, 7, 7, 7};
+    std::memset(h_A, 0, sizeof(double) * (size_t)N * N);
+    for (int i = 0; i < N; ++i) {
+        h_A[(size_t)i * N + i] += -P.D * tb.lam[i] - 0.5 * P.p4 * tb.wdiag[i];
+        for (int k = 0; k < FP_NSLOT; ++k) {
+            int j = tb.src[i * FP_NSLOT + k];
+            if (j < 0 || j >= N) continue;
+            h_A[(size_t)i * N + j] += s[grp[k]] * tb.coef[i * FP_NSLOT + k];
+        }
+    }
+    fp_free_tables(&tb);
+    return FP_OK;
+}

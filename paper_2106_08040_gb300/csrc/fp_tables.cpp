@@ -1,0 +1,363 @@
+// Closed-form coupling coefficients of the Fokker-Planck operator (Sec. 2.1,
+// Eq. FP-general with the drift of Eq. convection) in a real spherical-harmonic
+// basis, easy-axis frame (n = z).  Host code, FP64.
+//
+// Basis: Y_{l,0} = Q_l^0(z); Y_{l,m} = sqrt2 Q_l^m cos(m p); Y_{l,-m} = sqrt2 Q_l^m sin(m p)
+// (orthonormal, no Condon-Shortley phase), flat index l*l + l + m.
+//
+// With R = m x grad (rotation generators) and M_k = multiplication by m_k, the
+// operator of dc/dt = A c is
+//   A = -D Lap - p3 M_z R_z - (p4/2) W - sum_k p1 B_k R_k - sum_k p2 B_k G_k
+// where, for u = m_k and w = (n.m)^2 = z^2 (identities on the sphere:
+// Lap m_k = -2 m_k, Lap w = -6 w + 2, div(f grad u) = (Lap(uf) - u Lap f + f Lap u)/2):
+//   G_k Y_l = -(l+2) Proj_{l+1}(m_k Y_l) + (l-1) Proj_{l-1}(m_k Y_l)
+//   W Y_l   = sum_{l'=l,l+-2} [ (l(l+1) - l'(l'+1))/2 - 3 ] Proj_{l'}(w Y_l) + Y_l
+// Precession: div((H x m) f) = H . R f, and div((n.m)(n x m) f) = (n.m)(n.R) f.
+//
+// Closed forms used:
+//   z Y_{l,m} = a(l,|m|) Y_{l+1,m} + a(l-1,|m|) Y_{l-1,m},
+//       a(l, mu) = sqrt(((l+1)^2 - mu^2) / ((2l+1)(2l+3)))
+//   R_z Y_{l,m} = -m Y_{l,-m} (m > 0), R_z Y_{l,-m} = m Y_{l,m}
+//   R_x, R_y from the angular-momentum ladder operators of the complex basis
+//       (L+- Y^m = sqrt((l -+ m)(l +- m + 1)) Y^{m+-1}, R = i L), transformed
+//       to the real basis per degree l;
+//   x = [M_z, R_y]-form: M_x = M_z R_y - R_y M_z, M_y = R_x M_z - M_z R_x
+//       (since R_y z = -x, R_x z = y).
+#include <complex>
+#include <map>
+#include <vector>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include "fp_internal.h"
+
+namespace {
+
+typedef std::map<std::pair<int, int>, double> SpMat;   // (target, source) -> value
+
+inline int gi(int l, int m) { return l * l + l + m; }
+inline void lm_of(int i, int& l, int& m) {
+    l = (int)std::floor(std::sqrt((double)i) + 1e-9);
+    while ((l + 1) * (l + 1) <= i) ++l;
+    while (l * l > i) --l;
+    m = i - l * l - l;
+}
+
+double a_coef(int l, int mu) {
+    if (l < 0 || l < mu) return 0.0;
+    return std::sqrt((double)((l + 1) * (l + 1) - mu * mu) / (double)((2 * l + 1) * (2 * l + 3)));
+}
+
+// multiplication by z, degrees 0..Lmax (targets may reach Lmax+1)
+SpMat build_Mz(int Lmax) {
+    SpMat M;
+    for (int l = 0; l <= Lmax; ++l)
+        for (int m = -l; m <= l; ++m) {
+            int mu = std::abs(m);
+            double up = a_coef(l, mu), dn = a_coef(l - 1, mu);
+            if (up != 0.0) M[{gi(l + 1, m), gi(l, m)}] = up;
+            if (l - 1 >= mu && dn != 0.0) M[{gi(l - 1, m), gi(l, m)}] = dn;
+        }
+    return M;
+}
+
+SpMat build_Rz(int Lmax) {
+    SpMat R;
+    for (int l = 0; l <= Lmax; ++l)
+        for (int m = 1; m <= l; ++m) {
+            R[{gi(l, -m), gi(l, m)}] = -(double)m;
+            R[{gi(l, m), gi(l, -m)}] = (double)m;
+        }
+    return R;
+}
+
+// R_x and R_y in the real basis, per degree l, via the complex ladder operators.
+void build_Rxy(int Lmax, SpMat& Rx, SpMat& Ry) {
+    typedef std::complex<double> cd;
+    const cd I(0.0, 1.0);
+    const double s2 = std::sqrt(2.0);
+    for (int l = 0; l <= Lmax; ++l) {
+        int n = 2 * l + 1;
+        auto ci = [l](int m) { return m + l; };            // complex index
+        std::vector<cd> Rxc(n * n, 0.0), Ryc(n * n, 0.0);  // [target][source]
+        for (int m = -l; m <= l; ++m) {
+            if (m + 1 <= l) {
+                double lp = std::sqrt((double)(l - m) * (l + m + 1));
+                Rxc[ci(m + 1) * n + ci(m)] += I * 0.5 * lp;
+                Ryc[ci(m + 1) * n + ci(m)] += 0.5 * lp;
+            }
+            if (m - 1 >= -l) {
+                double lm = std::sqrt((double)(l + m) * (l - m + 1));
+                Rxc[ci(m - 1) * n + ci(m)] += I * 0.5 * lm;
+                Ryc[ci(m - 1) * n + ci(m)] += -0.5 * lm;
+            }
+        }
+        // U[a][m]: real function a = sum_m U[a][m] Y^m (complex, CS phase)
+        std::vector<cd> U(n * n, 0.0);
+        U[ci(0) * n + ci(0)] = 1.0;
+        for (int mu = 1; mu <= l; ++mu) {
+            double sg = (mu % 2) ? -1.0 : 1.0;
+            U[ci(mu) * n + ci(mu)] = sg / s2;
+            U[ci(mu) * n + ci(-mu)] = 1.0 / s2;
+            U[ci(-mu) * n + ci(mu)] = sg / (s2 * I);
+            U[ci(-mu) * n + ci(-mu)] = -1.0 / (s2 * I);
+        }
+        // R Y_a = sum_m U[a][m] sum_m' Rc[m'][m] Y^m', Y^m' = sum_b conj(U[b][m']) Y_b
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                cd sx = 0.0, sy = 0.0;
+                for (int m = 0; m < n; ++m) {
+                    if (U[a * n + m] == cd(0.0)) continue;
+                    for (int mp = 0; mp < n; ++mp) {
+                        cd v = std::conj(U[b * n + mp]) * U[a * n + m];
+                        sx += v * Rxc[mp * n + m];
+                        sy += v * Ryc[mp * n + m];
+                    }
+                }
+                int ta = gi(l, b - l), so = gi(l, a - l);   // target b, source a
+                if (std::abs(sx) > 1e-13) Rx[{ta, so}] = sx.real();
+                if (std::abs(sy) > 1e-13) Ry[{ta, so}] = sy.real();
+            }
+    }
+}
+
+SpMat matmul(const SpMat& A, const SpMat& B) {      // (A B)[t][s] = sum_k A[t][k] B[k][s]
+    std::map<int, std::vector<std::pair<int, double>>> Bcol;   // k -> (s, val) rows of B by k
+    for (auto& e : B) Bcol[e.first.first].push_back({e.first.second, e.second});
+    SpMat C;
+    for (auto& e : A) {
+        auto it = Bcol.find(e.first.second);
+        if (it == Bcol.end()) continue;
+        for (auto& bs : it->second) C[{e.first.first, bs.first}] += e.second * bs.second;
+    }
+    return C;
+}
+
+SpMat sub(const SpMat& A, const SpMat& B) {
+    SpMat C = A;
+    for (auto& e : B) C[e.first] -= e.second;
+    return C;
+}
+
+}  // namespace
+
+int fp_build_tables(int L, FpTablesHost* out) {
+    const int N = (L + 1) * (L + 1);
+    std::memset(out, 0, sizeof(*out));
+    out->L = L;
+    out->N = N;
+    out->coef = (double*)std::calloc((size_t)N * FP_NSLOT, sizeof(double));
+    out->src = (int*)std::malloc((size_t)N * FP_NSLOT * sizeof(int));
+    out->lam = (double*)std::calloc(N, sizeof(double));
+    out->wdiag = (double*)std::calloc(N, sizeof(double));
+    out->tslot = (int*)std::malloc((size_t)N * FP_NSLOT * sizeof(int));
+    if (!out->coef || !out->src || !out->lam || !out->wdiag || !out->tslot) { fp_free_tables(out); return FP_ENOMEM; }
+    for (int i = 0; i < N * FP_NSLOT; ++i) { out->src[i] = -1; out->tslot[i] = -1; }
+
+    SpMat Mz = build_Mz(L + 1);
+    SpMat Rz = build_Rz(L + 1);
+    SpMat Rx, Ry;
+    build_Rxy(L + 1, Rx, Ry);
+    SpMat Mx = sub(matmul(Mz, Ry), matmul(Ry, Mz));
+    SpMat My = sub(matmul(Rx, Mz), matmul(Mz, Rx));
+    SpMat Mz2 = matmul(Mz, Mz);
+    SpMat ZRz = matmul(Mz, Rz);
+
+    auto in_range = [N](int t, int s) { return t < N && s < N; };
+    auto put = [&](int t, int slot, int s, double v) {
+        out->coef[t * FP_NSLOT + slot] = v;
+        out->src[t * FP_NSLOT + slot] = s;
+    };
+    for (int t = 0; t < N; ++t) {
+        int l, m;
+        lm_of(t, l, m);
+        out->lam[t] = (double)l * (l + 1);
+    }
+    // W (anisotropy damping) from z^2
+    for (auto& e : Mz2) {
+        int t = e.first.first, s = e.first.second;
+        if (!in_range(t, s)) continue;
+        int lt, mt, ls, ms;
+        lm_of(t, lt, mt); lm_of(s, ls, ms);
+        double f = 0.5 * ((double)ls * (ls + 1) - (double)lt * (lt + 1)) - 3.0;
+        double v = e.second * f;
+        if (lt == ls) out->wdiag[t] = v + 1.0;
+        else if (lt == ls + 2) put(t, SL_W + 0, s, v);
+        else if (lt == ls - 2) put(t, SL_W + 1, s, v);
+    }
+    for (auto& e : ZRz) {
+        int t = e.first.first, s = e.first.second;
+        if (!in_range(t, s) || e.second == 0.0) continue;
+        int lt, mt, ls, ms;
+        lm_of(t, lt, mt); lm_of(s, ls, ms);
+        put(t, lt == ls + 1 ? SL_ZR + 0 : SL_ZR + 1, s, e.second);
+    }
+    for (auto& e : Rz) {
+        int t = e.first.first, s = e.first.second;
+        if (in_range(t, s)) put(t, SL_RZ, s, e.second);
+    }
+    auto put_lat = [&](const SpMat& R, int base) {       // same-l, |m| +- 1
+        for (auto& e : R) {
+            int t = e.first.first, s = e.first.second;
+            if (!in_range(t, s) || std::fabs(e.second) < 1e-15) continue;
+            int lt, mt, ls, ms;
+            lm_of(t, lt, mt); lm_of(s, ls, ms);
+            put(t, base + (std::abs(ms) < std::abs(mt) ? 0 : 1), s, e.second);
+        }
+    };
+    put_lat(Rx, SL_RX);
+    put_lat(Ry, SL_RY);
+    auto put_G = [&](const SpMat& M, int base, bool same_m) {
+        for (auto& e : M) {
+            int t = e.first.first, s = e.first.second;
+            if (!in_range(t, s) || std::fabs(e.second) < 1e-15) continue;
+            int lt, mt, ls, ms;
+            lm_of(t, lt, mt); lm_of(s, ls, ms);
+            double f = (lt == ls + 1) ? -(double)(ls + 2) : (double)(ls - 1);
+            if (f == 0.0) continue;
+            int slot;
+            if (same_m) slot = base + (lt == ls + 1 ? 0 : 1);          // source l-1 / l+1
+            else slot = base + 2 * (lt == ls + 1 ? 0 : 1) + (std::abs(ms) < std::abs(mt) ? 0 : 1);
+            put(t, slot, s, e.second * f);
+        }
+    };
+    put_G(Mz, SL_GZ, true);
+    put_G(Mx, SL_GX, false);
+    put_G(My, SL_GY, false);
+    // transpose slot of every lateral (|m| +- 1) coupling: the slot of row `src`
+    // whose source is the present row (the coupling pattern is symmetric)
+    for (int t = 0; t < N; ++t)
+        for (int k = SL_RX; k < FP_NSLOT; ++k) {
+            if (k >= SL_GZ && k < SL_GX) continue;
+            int s = out->src[t * FP_NSLOT + k];
+            if (s < 0) continue;
+            for (int k2 = SL_RX; k2 < FP_NSLOT; ++k2)
+                if (out->src[s * FP_NSLOT + k2] == t) { out->tslot[t * FP_NSLOT + k] = k2; break; }
+        }
+    return FP_OK;
+}
+
+void fp_free_tables(FpTablesHost* t) {
+    std::free(t->coef); std::free(t->src); std::free(t->lam); std::free(t->wdiag); std::free(t->tslot);
+    t->coef = nullptr; t->src = nullptr; t->lam = nullptr; t->wdiag = nullptr; t->tslot = nullptr;
+}
+
+// ---- Radau IIA(5) constants from the collocation definition ----------------
+namespace {
+void inv3(const double A[3][3], double B[3][3]) {
+    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+               - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+               + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    B[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
+    B[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+    B[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+    B[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
+    B[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+    B[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+    B[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
+    B[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+    B[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+}
+}  // namespace
+
+void fp_build_radau(FpRadau* r) {
+    typedef std::complex<double> cd;
+    const double s6 = std::sqrt(6.0);
+    // right Radau points on [0,1] for s = 3: zeros of d^2/dx^2 [x^2 (x-1)^3]
+    //   = 20x^3 - 36x^2 + 18x - 2 = 2 (x - 1)(10x^2 - 8x + 1)
+    r->c[0] = (4.0 - s6) / 10.0;
+    r->c[1] = (4.0 + s6) / 10.0;
+    r->c[2] = 1.0;
+    // a_ij = int_0^{c_i} l_j(x) dx, l_j quadratic Lagrange basis on the nodes
+    for (int j = 0; j < 3; ++j) {
+        int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
+        double den = (r->c[j] - r->c[k1]) * (r->c[j] - r->c[k2]);
+        double q2 = 1.0 / den, q1 = -(r->c[k1] + r->c[k2]) / den, q0 = r->c[k1] * r->c[k2] / den;
+        for (int i = 0; i < 3; ++i) {
+            double x = r->c[i];
+            r->a[i][j] = q2 * x * x * x / 3.0 + q1 * x * x / 2.0 + q0 * x;
+        }
+    }
+    double ai[3][3];
+    inv3(r->a, ai);
+    // eigenvalues of a^{-1}: lambda^3 - t1 lambda^2 + t2 lambda - t3 = 0
+    double t1 = ai[0][0] + ai[1][1] + ai[2][2];
+    double t2 = ai[0][0] * ai[1][1] - ai[0][1] * ai[1][0] + ai[0][0] * ai[2][2] - ai[0][2] * ai[2][0]
+              + ai[1][1] * ai[2][2] - ai[1][2] * ai[2][1];
+    double t3 = ai[0][0] * (ai[1][1] * ai[2][2] - ai[1][2] * ai[2][1])
+              - ai[0][1] * (ai[1][0] * ai[2][2] - ai[1][2] * ai[2][0])
+              + ai[0][2] * (ai[1][0] * ai[2][1] - ai[1][1] * ai[2][0]);
+    double g = t1;                                   // Newton from above on the real root
+    for (int it = 0; it < 200; ++it) {
+        double f = ((g - t1) * g + t2) * g - t3, df = (3.0 * g - 2.0 * t1) * g + t2;
+        double dg = f / df;
+        g -= dg;
+        if (std::fabs(dg) < 1e-16 * std::fabs(g)) break;
+    }
+    // deflate: lambda^2 - (t1 - g) lambda + t3/g = 0
+    double bq = t1 - g, cq = t3 / g;
+    double alp = 0.5 * bq, bet = std::sqrt(cq - alp * alp);
+    r->gam = g; r->alp = alp; r->bet = bet;
+    // eigenvectors: real one and complex one (for alp + i bet) via cross products
+    auto null_real = [&](double lam, double v[3]) {
+        double M[3][3];
+        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) M[i][j] = ai[i][j] - (i == j ? lam : 0.0);
+        v[0] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+        v[1] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+        v[2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    };
+    double vr[3];
+    null_real(g, vr);
+    cd lam(alp, bet), M[3][3], vc[3];
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) M[i][j] = ai[i][j] - (i == j ? lam : cd(0.0));
+    vc[0] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+    vc[1] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+    vc[2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    for (int i = 0; i < 3; ++i) {
+        r->T[i][0] = vr[i];
+        r->T[i][1] = vc[i].real();
+        r->T[i][2] = vc[i].imag();
+    }
+    inv3(r->T, r->Ti);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += r->Ti[i][k] * ai[k][j];
+            r->K[i][j] = s;
+        }
+    // embedded order-3 formula with an explicit stage at t_n of weight g0 = 1/gam:
+    // sum_{i>=0} bh_i c_i^{q-1} = 1/q (q = 1, 2, 3) with c_0 = 0, bh_0 = g0
+    r->g0 = 1.0 / g;
+    double V[3][3], Vi[3][3], rhs[3] = {1.0 - r->g0, 0.5, 1.0 / 3.0}, bh[3];
+    for (int q = 0; q < 3; ++q) for (int i = 0; i < 3; ++i) V[q][i] = std::pow(r->c[i], q);
+    inv3(V, Vi);
+    for (int i = 0; i < 3; ++i) bh[i] = Vi[i][0] * rhs[0] + Vi[i][1] * rhs[1] + Vi[i][2] * rhs[2];
+    // e = (bh - b)^T a^{-1}, b = last row of a
+    for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) s += (bh[i] - r->a[2][i]) * ai[i][j];
+        r->e[j] = s;
+    }
+}
+
+// Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n.
+void fp_gauss_legendre(int n, double* x, double* w) {
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}

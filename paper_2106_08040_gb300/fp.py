@@ -1,0 +1,172 @@
+"""Python binding of libfp.so with the C-ABI names (include/fp.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels.
+Device buffers are torch CUDA tensors (torch supplies memory and streams).
+"""
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, fp_drive, fp_instance, fp_material, fp_tol
+
+INSTANCE_DTYPE = np.dtype([("h_off", "<f8", (3,)), ("theta", "<f8"), ("phi", "<f8"), ("K", "<f8"),
+                           ("d", "<f8"), ("L", "<i4"), ("flags", "<i4")])
+assert INSTANCE_DTYPE.itemsize == 64
+
+
+@dataclass(frozen=True)
+class Material:
+    """Sec. 2.1 material constants (SI)."""
+    Ms: float = 474e3
+    alpha: float = 0.1
+    gamma: float = 1.76e11
+    T_B: float = 293.0
+
+    def c(self):
+        return fp_material(self.Ms, self.alpha, self.gamma, self.T_B)
+
+
+@dataclass(frozen=True)
+class Drive:
+    """B_k(t) = amp_k sin(2 pi freq_k t + phase_k) [T]; sampling schedule."""
+    amp: tuple
+    freq: tuple
+    phase: tuple
+    period: float
+    samples_per_period: int
+    warmup_periods: int
+    output_periods: int
+
+    def c(self):
+        d = fp_drive()
+        for k in range(3):
+            d.amp[k], d.freq[k], d.phase[k] = self.amp[k], self.freq[k], self.phase[k]
+        d.period = self.period
+        d.samples_per_period = self.samples_per_period
+        d.warmup_periods = self.warmup_periods
+        d.output_periods = self.output_periods
+        return d
+
+    @property
+    def num_samples(self):
+        return self.output_periods * self.samples_per_period
+
+
+@dataclass(frozen=True)
+class Tol:
+    rtol: float = 1e-9
+    atol: float = 1e-15
+    max_steps: int = 2_000_000
+    newton_max_iter: int = 8
+    refactor_every: int = 4
+    checkpoint_every: int = 64
+
+    def c(self):
+        return fp_tol(self.rtol, self.atol, self.max_steps, self.newton_max_iter,
+                      self.refactor_every, self.checkpoint_every)
+
+
+def fp_max_degree():
+    return _lib.lib().fp_max_degree()
+
+
+class Context:
+    """Owns an fp_ctx (coefficient tables on the current CUDA device)."""
+
+    def __init__(self, material: Material, drive: Drive, tol: Tol, L_max: int):
+        self.material, self.drive, self.tol, self.L_max = material, drive, tol, L_max
+        h = C.c_void_p()
+        m, d, t = material.c(), drive.c(), tol.c()
+        check(_lib.lib().fp_setup(C.byref(m), C.byref(d), C.byref(t), int(L_max), C.byref(h)), "fp_setup")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("context destroyed")
+        return self._h
+
+    def num_samples(self):
+        return _lib.lib().fp_num_samples(self.handle)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().fp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fp_setup(material: Material, drive: Drive, tol: Tol, L_max: int) -> Context:
+    return Context(material, drive, tol, L_max)
+
+
+def fp_destroy(ctx: Context):
+    ctx.close()
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def instances_to_device(inst: np.ndarray, device="cuda"):
+    """Pack a structured INSTANCE_DTYPE array into a device byte tensor."""
+    import torch
+    arr = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
+    host = torch.from_numpy(arr.view(np.uint8).reshape(-1).copy())
+    return host.to(device)
+
+
+def fp_solve_batch(ctx: Context, d_inst, n: int, d_m=None, d_dmdt=None, d_status=None, d_stats=None, stream=None):
+    """Launch the batched solve; buffers are torch CUDA tensors (float64 [n,S,3],
+    int32 [n], int32 [n,4])."""
+    check(_lib.lib().fp_solve_batch(ctx.handle, _ptr(d_inst), int(n), _ptr(d_m), _ptr(d_dmdt), _ptr(d_status),
+                                    _ptr(d_stats), _stream_ptr(stream)), "fp_solve_batch")
+
+
+def fp_signal(ctx: Context, d_dmdt, n: int, k_max: int, channels, d_phihat, stream=None):
+    ch = np.ascontiguousarray(np.asarray(channels, dtype=np.float64).reshape(-1, 3))
+    check(_lib.lib().fp_signal(ctx.handle, _ptr(d_dmdt), int(n), int(k_max),
+                               ch.ctypes.data_as(C.POINTER(C.c_double)), int(ch.shape[0]), _ptr(d_phihat),
+                               _stream_ptr(stream)), "fp_signal")
+
+
+def fp_operator_dense(material: Material, L: int, K: float, d: float, B_nframe):
+    """Dense easy-axis-frame Galerkin matrix (host only, no GPU)."""
+    N = (L + 1) ** 2
+    out = np.zeros((N, N))
+    inst = fp_instance()
+    inst.L, inst.K, inst.d = int(L), float(K), float(d)
+    B = (C.c_double * 3)(*[float(x) for x in B_nframe])
+    m = material.c()
+    check(_lib.lib().fp_operator_dense(C.byref(m), C.byref(inst), B, out.ctypes.data_as(C.POINTER(C.c_double))),
+          "fp_operator_dense")
+    return out
+
+
+def solve(ctx: Context, inst: np.ndarray, want_m=True, want_dmdt=True, stream=None):
+    """Convenience: solve host instance records on the current device.
+    Returns torch tensors (m, dmdt, status, stats) on the device."""
+    import torch
+    n = len(inst)
+    S = ctx.num_samples()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_inst = instances_to_device(inst, dev)
+    m = torch.empty((n, S, 3), dtype=torch.float64, device=dev) if want_m else None
+    dm = torch.empty((n, S, 3), dtype=torch.float64, device=dev) if want_dmdt else None
+    st = torch.empty((n,), dtype=torch.int32, device=dev)
+    stats = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    fp_solve_batch(ctx, d_inst, n, m, dm, st, stats, stream=stream)
+    return m, dm, st, stats
