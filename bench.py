@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the batched Neel Fokker-Planck solve on GB300.
+
+Workload (default): the 32 x 32-voxel system-matrix batch -- cosine Lissajous
+drive 12 mT per axis, f_x = 2.5 MHz/102, f_y = 2.5 MHz/96, 1632 samples per
+652.8 us period, selection gradient diag(-1, -1, 2) T/m over 24 x 24 mm, easy
+axis along x, K = 2e3 J/m^3, d = 20 nm, truncation L = 16; every instance is
+integrated over 1 warm-up + 1 output period (2 instance-periods) and its
+phi_hat harmonics computed.  One step = fp_solve_batch + fp_signal over the
+batch, inputs resident in HBM.  Metric: instance-periods/s (whole job).
+
+Multi-GPU (torchrun, one rank per GPU): weak scaling, rank r solves the same
+voxel batch for easy-axis angle vartheta_r = 15 deg * r (the paper's angle set),
+no collective on the data path; barrier + max-over-ranks timing.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on
+a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP instance-periods/s at ≤1e-9 rel err vs FP64 oracle; surrogate speedup at 1e-3"
+UNIT = "instance-periods/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--stages", type=int, default=3)
+    p.add_argument("--rtol", type=float, default=1e-9)
+    p.add_argument("--cpu-sample-s", type=float, default=20.0, help="target CPU seconds per oracle process")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_for_rank(rank):
+    from paper_2106_08040_gb300 import workloads
+    dspec, inst = workloads.system_matrix_workload()
+    inst["phi"] = np.deg2rad(15.0 * (rank % 12))
+    return dspec, inst
+
+
+# ----------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------- flop accounting ----
+def fp64_flops_per_instance(stats, N, nnz, S):
+    """Algorithmic FP64 flops of one instance from the kernel's own counters:
+    every Newton iteration applies A at S stage values (2 nnz each) and forms
+    S residuals (S^2 + S multiply-adds per entry) and S stage updates; every
+    accepted or rejected step adds the error combination (S + 1 per entry),
+    and every accepted step one more apply for f(t, y) and the state update."""
+    steps, rej, iters = stats[:, 0].astype(np.float64), stats[:, 1].astype(np.float64), stats[:, 2].astype(np.float64)
+    per_iter = S * 2.0 * nnz + N * (2.0 * S * S + 3.0 * S)
+    per_try = N * 2.0 * (S + 1)
+    per_acc = 2.0 * nnz + N
+    return iters * per_iter + (steps + rej) * per_try + steps * per_acc
+
+
+def operator_nnz(fp, L):
+    A = fp.fp_operator_dense(fp.Material(), L, 2e3, 20e-9, [0.003, -0.002, 0.004])
+    return int(np.count_nonzero(A))
+
+
+# -------------------------------------------------------------- CPU oracle ----
+def _oracle_window(args):
+    """One bounded oracle solve: voxel k of the workload, first `ns` samples."""
+    import os as _os
+    _os.environ.setdefault("OMP_NUM_THREADS", "1")
+    (dspec_d, rec, ns, rtol) = args
+    from oracle import physics, solve
+    drive = physics.Drive(amp=dspec_d["amp"], freq=dspec_d["freq"], phase=dspec_d["phase"], period=dspec_d["period"])
+    sched = solve.Schedule(dspec_d["samples_per_period"], 0, 1)
+    inst = solve.Instance(h_off=tuple(rec["h_off"]), theta=float(rec["theta"]), phi=float(rec["phi"]),
+                          K=float(rec["K"]), d=float(rec["d"]), L=int(rec["L"]))
+    P = physics.derive(physics.Material(), inst.K, inst.d)
+    from oracle import galerkin, radau
+    n = physics.easy_axis(inst.theta, inst.phi)
+    t0 = time.time()
+    A0, A1 = galerkin.weak_form_matrices(inst.L, P, n)
+    off = np.asarray(inst.h_off)
+
+    def A_of_t(t):
+        B = drive.field(t, off)
+        return A0 + B[0] * A1[0] + B[1] * A1[1] + B[2] * A1[2]
+
+    c0 = galerkin.boltzmann_coeffs(inst.L, P, n, drive.field(0.0, off))
+    T_s = drive.period / sched.samples_per_period
+    t_out = (np.arange(ns) + 1) * T_s
+    integ = radau.RadauIIA(A_of_t, rtol=rtol, h0=min(T_s, 0.01 * P.tau), h_max=T_s)
+    integ.integrate(0.0, c0, t_out)
+    return time.time() - t0, ns / dspec_d["samples_per_period"], integ.n_steps
+
+
+def cpu_oracle_sample(dspec, inst, target_s, rtol=1e-10):
+    """Oracle on all host cores (spawned single-threaded processes), each over the
+    first samples of one voxel's period; throughput scaled to instance-periods/s."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    dd = dict(amp=dspec.amp, freq=dspec.freq, phase=dspec.phase, period=dspec.period,
+              samples_per_period=dspec.samples_per_period)
+    # calibrate the window on one process: 4 samples
+    rng = np.random.default_rng(0)
+    picks = rng.choice(len(inst), size=cores, replace=False)
+    el, frac, _ = _oracle_window((dd, inst[picks[0]], 4, rtol))
+    per_sample = max(el / 4, 1e-3)
+    ns = int(max(4, min(dspec.samples_per_period, target_s / per_sample)))
+    ctx = mp.get_context("spawn")
+    t0 = time.time()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_window, [(dd, inst[k], ns, rtol) for k in picks])
+    wall = time.time() - t0
+    ip = sum(r[1] for r in res)
+    return {"value": ip / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d voxels of the 32x32 L=16 batch, first %d of 1632 samples of the first period each "
+                      "(Radau IIA rtol 1e-10, one process per core); %.3f instance-periods in %.1f s wall"
+                      % (cores, ns, ip, wall)}
+
+
+# ------------------------------------------------------------------ GPU arm --
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2106_08040_gb300 import build
+    rank, world, local = dist_env()
+    if world > 1:
+        os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    from paper_2106_08040_gb300 import fp
+    dspec, inst = workload_for_rank(rank)
+    n = len(inst)
+    L = int(inst["L"][0])
+    drv = fp.Drive(**dspec.__dict__)
+    tol = fp.Tol(rtol=args.rtol, stages=args.stages)
+    ctx = fp.Context(fp.Material(), drv, tol, L)
+    S_out = ctx.num_samples()
+    K = 816
+    C = 2
+    ch = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    dev = torch.device("cuda", local)
+    d_inst = fp.instances_to_device(inst, dev)
+    m = torch.empty((n, S_out, 3), dtype=torch.float64, device=dev)
+    dm = torch.empty_like(m)
+    st = torch.empty((n,), dtype=torch.int32, device=dev)
+    stats = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    ph = torch.empty((n, C, K + 1, 2), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fp.fp_solve_batch(ctx, d_inst, n, m, dm, st, stats, stream=stream)
+        fp.fp_signal(ctx, dm, n, K, ch, ph, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    peak = fp.fp_peak_fp64()
+    nnz = operator_nnz(fp, L)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))                        # evict L2 between timed steps (not timed)
+        a, b, c = ev[k]
+        a.record(stream)
+        fp.fp_solve_batch(ctx, d_inst, n, m, dm, st, stats, stream=stream)
+        b.record(stream)
+        fp.fp_signal(ctx, dm, n, K, ch, ph, stream=stream)
+        c.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    solve_ms = [a.elapsed_time(b) for a, b, c in ev]
+    ms = sum(step_ms) / args.steps
+    t_solve = sum(solve_ms) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    status = st.cpu().numpy()
+    sts = stats.cpu().numpy()
+    periods = drv.warmup_periods + drv.output_periods
+    value = world * n * periods / (ms * 1e-3)
+    # roofline of the dominant kernel (the solver): FP64 pipe
+    flops = float(fp64_flops_per_instance(sts, (L + 1) ** 2, nnz, args.stages).sum())
+    achieved = flops / (t_solve * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak / 1e3, "unit": "TFLOP/s",
+            "frac": achieved / (peak / 1e3), "traffic": None,
+            "kernel": "fp_solve_kernel<%d> (FP64 pipe)" % args.stages,
+            "peak_source": "measured FP64 FMA throughput (fp_peak_fp64, this GPU, this run)"}
+    # end-to-end through the public API: host instances -> solve -> phi_hat -> host
+    h_inst = torch.from_numpy(np.ascontiguousarray(inst).view(np.uint8).reshape(-1).copy()).pin_memory()
+    h_ph = torch.empty(ph.shape, dtype=ph.dtype).pin_memory()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        d_inst.copy_(h_inst, non_blocking=True)
+        step()
+        h_ph.copy_(ph, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "system_matrix_32x32_L16_lissajous", "instances_per_gpu": n, "L": L,
+                       "periods_per_instance": periods, "samples_per_period": drv.samples_per_period,
+                       "radau_stages": args.stages, "rtol": args.rtol, "harmonics": K + 1, "channels": C,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": "independent instances; weak scaling, rank r uses easy-axis angle 15 deg*r"},
+            "gpu_launches": 2 * args.steps,
+            "e2e": {"value": world * n * periods / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h_inst.numel()), "d2h_bytes_per_step": int(h_ph.numel() * 8)},
+            "roofline": roof,
+            "clocks": clk,
+            "solver_ms_per_step": t_solve,
+            "status_ok": int((status == 0).sum()), "status_total": int(status.size),
+            "solver_counters": {"steps_mean": float(sts[:, 0].mean()), "rejected_mean": float(sts[:, 1].mean()),
+                                "newton_iters_mean": float(sts[:, 2].mean()), "factorisations_mean": float(sts[:, 3].mean()),
+                                "fp64_flops_per_step": flops},
+        }
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out, dspec, inst
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        from paper_2106_08040_gb300 import workloads
+        dspec, inst = workloads.system_matrix_workload()
+        vals = []
+        t_all = time.time()
+        for k in range(args.warmup + args.steps):
+            r = cpu_oracle_sample(dspec, inst, args.cpu_sample_s / 2)
+            if k >= args.warmup:
+                vals.append(r)
+        wall = time.time() - t_all
+        v = statistics.mean(x["value"] for x in vals)
+        cb = dict(vals[-1])
+        cb["value"] = v
+        out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * wall / (args.warmup + args.steps),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "impl": "reference",
+               "config": {"workload": "system_matrix_32x32_L16_lissajous", "instances_per_gpu": len(inst), "L": 16,
+                          "periods_per_instance": 2, "samples_per_period": 1632},
+               "cpu_baseline": cb,
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return 0
+    out, dspec, inst = run_gpu(args)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_oracle_sample(dspec, inst, args.cpu_sample_s)
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -26,7 +26,7 @@
  * Discretisation: real spherical-harmonic Galerkin expansion of f truncated at
  * degree L (N = (L+1)^2 coefficients), the operator applied matrix-free from
  * closed-form coupling coefficients in the easy-axis frame.  Time integration:
- * 3-stage Radau IIA (order 5, L-stable) with per-instance adaptive steps,
+ * Radau IIA (3 stages, order 5, or 5 stages, order 9; L-stable) with per-instance adaptive steps,
  * simplified Newton iterations whose residuals are FP64 and whose iteration
  * matrices are factorised in FP32.  Initial state: Boltzmann equilibrium at
  * H(0) including the anisotropy.
@@ -90,13 +90,16 @@ typedef struct {
 /* Integrator controls.  Local error per step (max norm) must stay below
  * atol + rtol * max|c|.  max_steps bounds accepted+rejected steps per
  * instance; newton_max_iter bounds Newton iterations per step;
- * refactor_every bounds how many steps reuse one FP32 factorisation. */
+ * refactor_every bounds how many steps reuse one FP32 factorisation;
+ * stages selects the Radau IIA method: 3 (order 5) or 5 (order 9). */
 typedef struct {
     double rtol, atol;
     int max_steps;
     int newton_max_iter;
     int refactor_every;
     int checkpoint_every;   /* adjoint checkpoint stride in steps (fp_grad) */
+    int stages;
+    int pad_;
 } fp_tol;
 
 /* One instance (Sec. 2.2 (iii) model m_bar_(D, K, vartheta) at one voxel):
@@ -160,6 +163,12 @@ int fp_signal(fp_ctx* ctx, const double* d_dmdt, int n, int k_max,
  * i = l*l + l + m (real SH without Condon-Shortley phase). */
 int fp_operator_dense(const fp_material* mat, const fp_instance* h_inst,
                       const double B_nframe[3], double* h_A);
+
+/* Measurement utility (the paper has no counterpart): FP64 FMA throughput of
+ * the current device in GFLOP/s (2 flops per FMA), from 8 independent FMA
+ * chains per thread on 8 CTAs per SM.  Allocates and frees 32 KB of device
+ * memory; synchronous.  Used as the roofline denominator of the solver. */
+int fp_peak_fp64(double* gflops);
 
 /* Text for a status or error code, and the last error message. */
 const char* fp_status_str(int code);

@@ -13,7 +13,7 @@ FP_OK, FP_EINVAL, FP_ECUDA, FP_ENOMEM, FP_EUNSUPPORTED = 0, -1, -2, -3, -4
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT"}
 
 EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_solve_batch",
-            "fp_signal", "fp_operator_dense", "fp_status_str", "fp_last_error"]
+            "fp_signal", "fp_operator_dense", "fp_peak_fp64", "fp_status_str", "fp_last_error"]
 
 
 class fp_material(C.Structure):
@@ -28,7 +28,8 @@ class fp_drive(C.Structure):
 
 class fp_tol(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_steps", C.c_int),
-                ("newton_max_iter", C.c_int), ("refactor_every", C.c_int), ("checkpoint_every", C.c_int)]
+                ("newton_max_iter", C.c_int), ("refactor_every", C.c_int), ("checkpoint_every", C.c_int),
+                ("stages", C.c_int), ("pad_", C.c_int)]
 
 
 class fp_instance(C.Structure):
@@ -65,6 +66,8 @@ def lib():
     L.fp_signal.restype = i
     L.fp_operator_dense.argtypes = [C.POINTER(fp_material), C.POINTER(fp_instance), C.POINTER(d), C.POINTER(d)]
     L.fp_operator_dense.restype = i
+    L.fp_peak_fp64.argtypes = [C.POINTER(d)]
+    L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]
     L.fp_status_str.restype = C.c_char_p
     L.fp_last_error.restype = C.c_char_p

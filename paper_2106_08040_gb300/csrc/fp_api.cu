@@ -10,19 +10,11 @@
 #include <vector>
 #include "fp_internal.h"
 
-struct DevTab {
-    const double* coef;
-    const int* src;
-    const int* tslot;
-    const double* lam;
-    const double* wdiag;
-};
-
-size_t fp_solver_smem_bytes(int L);
-int fp_launch_solve(const DevTab* tab, const fp_material* mat, const fp_drive* drv, const fp_tol* tol,
-                    const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
+size_t fp_solver_smem_bytes(int stages, int L);
+int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
+                    const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
                     int* d_status, int* d_stats, int grid, cudaStream_t st);
-int fp_upload_constants(const FpRadau* r, const double* glx, const double* glw);
+int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw);
 
 struct fp_ctx {
     fp_material mat;
@@ -31,12 +23,13 @@ struct fp_ctx {
     int L_max;
     int device;
     int num_sms;
-    FpTablesHost host;        // kept for fp_operator_dense
+    FpTablesHost host;
     double* d_coef;
     int* d_src;
-    int* d_tslot;
     double* d_lam;
     double* d_wdiag;
+    DevBlk blk;               // device block structure, all degrees 2..L_max
+    void* d_blk_mem;          // one allocation backing blk
     double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
 };
 
@@ -83,7 +76,7 @@ int fp_destroy(fp_ctx* ctx) {
     if (!ctx) return FP_OK;
     cudaFree(ctx->d_coef);
     cudaFree(ctx->d_src);
-    cudaFree(ctx->d_tslot);
+    cudaFree(ctx->d_blk_mem);
     cudaFree(ctx->d_lam);
     cudaFree(ctx->d_wdiag);
     cudaFree(ctx->d_tw);
@@ -105,6 +98,8 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
     if (!(tol->rtol > 0) || !(tol->atol >= 0) || tol->max_steps < 1 || tol->newton_max_iter < 1 ||
         tol->refactor_every < 1)
         return fail(FP_EINVAL, "fp_setup: bad tolerances");
+    if (tol->stages != 3 && tol->stages != 5)
+        return fail(FP_EUNSUPPORTED, "fp_setup: stages=%d (3 or 5 supported)", tol->stages);
     fp_ctx* c = new (std::nothrow) fp_ctx();
     if (!c) return fail(FP_ENOMEM, "fp_setup: host allocation");
     c->mat = *mat;
@@ -124,7 +119,6 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
     };
     up((void**)&c->d_coef, c->host.coef, N * FP_NSLOT * sizeof(double));
     up((void**)&c->d_src, c->host.src, N * FP_NSLOT * sizeof(int));
-    up((void**)&c->d_tslot, c->host.tslot, N * FP_NSLOT * sizeof(int));
     up((void**)&c->d_lam, c->host.lam, N * sizeof(double));
     up((void**)&c->d_wdiag, c->host.wdiag, N * sizeof(double));
     std::vector<double> tw(2 * (size_t)drive->samples_per_period);
@@ -136,11 +130,65 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
     }
     up((void**)&c->d_tw, tw.data(), tw.size() * sizeof(double));
     if (rc != FP_OK) { fp_destroy(c); return rc; }
-    FpRadau r;
-    fp_build_radau(&r);
+    // block structure of every degree 2..L_max, packed into one device buffer
+    {
+        std::vector<FpBlkHost> bl(L_max + 1);
+        size_t rows = 0;
+        std::memset(c->blk.off, 0, sizeof(c->blk.off));
+        for (int L = 2; L <= L_max; ++L) {
+            if (fp_build_blocks(&c->host, L, &bl[L]) != FP_OK) {
+                for (int q = 2; q < L; ++q) fp_free_blocks(&bl[q]);
+                fp_destroy(c);
+                return fail(FP_ENOMEM, "fp_setup: block structure");
+            }
+            c->blk.off[L] = (int)rows;
+            rows += bl[L].N;
+        }
+        const size_t b_glob = rows * 4, b_u8 = rows * FP_NSB, b_f8 = rows * FP_NSB * 4, b_u6 = rows * FP_NLT,
+                     b_f6 = rows * FP_NLT * 4;
+        size_t offs[11], o = 0;
+        const size_t sizes[11] = {b_glob, b_u8, b_u8, b_f8, b_u6, b_u6, b_f6, b_u6, b_u6, b_f6, b_u6};
+        for (int q = 0; q < 11; ++q) { offs[q] = o; o += (sizes[q] + 255) & ~(size_t)255; }
+        std::vector<unsigned char> hb(o, 0);
+        for (int L = 2; L <= L_max; ++L) {
+            const FpBlkHost& b = bl[L];
+            const size_t r0 = c->blk.off[L];
+            std::memcpy(&hb[offs[0] + r0 * 4], b.glob, b.N * 4);
+            std::memcpy(&hb[offs[1] + r0 * FP_NSB], b.sb_k, b.N * FP_NSB);
+            std::memcpy(&hb[offs[2] + r0 * FP_NSB], b.sb_g, b.N * FP_NSB);
+            std::memcpy(&hb[offs[3] + r0 * FP_NSB * 4], b.sb_cf, b.N * FP_NSB * 4);
+            std::memcpy(&hb[offs[4] + r0 * FP_NLT], b.dn_k, b.N * FP_NLT);
+            std::memcpy(&hb[offs[5] + r0 * FP_NLT], b.dn_g, b.N * FP_NLT);
+            std::memcpy(&hb[offs[6] + r0 * FP_NLT * 4], b.dn_cf, b.N * FP_NLT * 4);
+            std::memcpy(&hb[offs[7] + r0 * FP_NLT], b.up_k, b.N * FP_NLT);
+            std::memcpy(&hb[offs[8] + r0 * FP_NLT], b.up_g, b.N * FP_NLT);
+            std::memcpy(&hb[offs[9] + r0 * FP_NLT * 4], b.up_cf, b.N * FP_NLT * 4);
+            std::memcpy(&hb[offs[10] + r0 * FP_NLT], b.dnT, b.N * FP_NLT);
+            fp_free_blocks(&bl[L]);
+        }
+        up(&c->d_blk_mem, hb.data(), o);
+        if (rc != FP_OK) { fp_destroy(c); return rc; }
+        unsigned char* base = (unsigned char*)c->d_blk_mem;
+        c->blk.glob = (const int*)(base + offs[0]);
+        c->blk.sb_k = base + offs[1];
+        c->blk.sb_g = base + offs[2];
+        c->blk.sb_cf = (const float*)(base + offs[3]);
+        c->blk.dn_k = base + offs[4];
+        c->blk.dn_g = base + offs[5];
+        c->blk.dn_cf = (const float*)(base + offs[6]);
+        c->blk.up_k = base + offs[7];
+        c->blk.up_g = base + offs[8];
+        c->blk.up_cf = (const float*)(base + offs[9]);
+        c->blk.dnT = base + offs[10];
+    }
+    FpRadau r3, r5;
+    if (fp_build_radau(3, &r3) != FP_OK || fp_build_radau(5, &r5) != FP_OK) {
+        fp_destroy(c);
+        return fail(FP_EINVAL, "fp_setup: Radau constants");
+    }
     double glx[FP_NGL], glw[FP_NGL];
     fp_gauss_legendre(FP_NGL, glx, glw);
-    if (fp_upload_constants(&r, glx, glw) != FP_OK) { fp_destroy(c); return fail(FP_ECUDA, "fp_setup: constants"); }
+    if (fp_upload_constants(&r3, &r5, glx, glw) != FP_OK) { fp_destroy(c); return fail(FP_ECUDA, "fp_setup: constants"); }
     *out = c;
     return FP_OK;
 }
@@ -156,15 +204,15 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     if (n < 0) return fail(FP_EINVAL, "fp_solve_batch: n < 0");
     if (n == 0) return FP_OK;
     if (!d_inst || !d_status) return fail(FP_EINVAL, "fp_solve_batch: NULL instance or status buffer");
-    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_tslot, ctx->d_lam, ctx->d_wdiag};
-    size_t sm = fp_solver_smem_bytes(ctx->L_max);
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag};
+    size_t sm = fp_solver_smem_bytes(ctx->tol.stages, ctx->L_max);
     int max_sm = 0;
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     if ((int)sm > max_sm)
         return fail(FP_EUNSUPPORTED, "fp_solve_batch: %zu bytes of shared memory needed, %d available", sm, max_sm);
     int grid = n < ctx->num_sms ? n : ctx->num_sms;
-    int rc = fp_launch_solve(&tab, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max, d_m, d_dmdt, d_status,
-                             d_stats, grid, (cudaStream_t)stream);
+    int rc = fp_launch_solve(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
+                             d_m, d_dmdt, d_status, d_stats, grid, (cudaStream_t)stream);
     if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }

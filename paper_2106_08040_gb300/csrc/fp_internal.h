@@ -61,16 +61,19 @@ FP_HD void fp_rotation(double th, double ph, double R[9]) {
     R[6] = st * cp; R[7] = st * sp; R[8] = ct;
 }
 
-// Coefficients of the 3-stage Radau IIA method and of its simplified-Newton
-// transformation and embedded error estimate (derived on the host).
+// Coefficients of an s-stage Radau IIA method (s = 3, 5, 7) and of its
+// simplified-Newton transformation and embedded error estimate (host-derived).
+#define FP_SMAX 7
 struct FpRadau {
-    double c[3];
-    double a[3][3];
-    double T[3][3];      // a^{-1} = T Lam T^{-1}
-    double Ti[3][3];
-    double K[3][3];      // Ti a^{-1} (= Lam Ti)
-    double gam, alp, bet;
-    double e[3], g0;     // err_pre = h g0 f(t_n, y_n) + sum_i e_i Z_i
+    int s;
+    double c[FP_SMAX];
+    double a[FP_SMAX][FP_SMAX];
+    double T[FP_SMAX][FP_SMAX];      // a^{-1} = T Lam T^{-1}
+    double Ti[FP_SMAX][FP_SMAX];
+    double K[FP_SMAX][FP_SMAX];      // Ti a^{-1}
+    double gam;                      // real eigenvalue of a^{-1}
+    double alp[3], bet[3];           // complex pairs alp +- i bet (bet > 0)
+    double e[FP_SMAX], g0;           // err_pre = h g0 f(t_n, y_n) + sum_i e_i Z_i
 };
 
 // Host-built tables (device copies live in the context).
@@ -86,5 +89,54 @@ struct FpTablesHost {
 
 int fp_build_tables(int L, FpTablesHost* out);     // returns 0 / FP_ENOMEM
 void fp_free_tables(FpTablesHost* t);
-void fp_build_radau(FpRadau* r);
+int fp_build_radau(int s, FpRadau* r);             // returns 0 / FP_EINVAL
+
+// Block structure of the Galerkin matrix for one degree L, rows in block order
+// (blocks mu = |m| = 0..L; block 0 = (l, 0) for l = 0..L, block mu > 0 =
+// (l, +mu), (l, -mu) interleaved for l = mu..L).  For every row: up to 7
+// couplings inside its block (sb), up to 6 to block mu-1 (dn) and up to 6 to
+// block mu+1 (up), each as (local column, scalar group, table coefficient);
+// dnT gives, for each dn partner, the position in the partner's up list of the
+// coupling back to this row (255 if that entry is structurally zero).
+#define FP_NSB 8
+#define FP_NLT 6
+struct FpBlkHost {
+    int L, N;
+    int* glob;                 // [N] natural index of block row b
+    unsigned char* sb_k;       // [N][FP_NSB]  (255 = none)
+    unsigned char* sb_g;
+    float* sb_cf;
+    unsigned char* dn_k;       // [N][FP_NLT]
+    unsigned char* dn_g;
+    float* dn_cf;
+    unsigned char* up_k;       // [N][FP_NLT]
+    unsigned char* up_g;
+    float* up_cf;
+    unsigned char* dnT;        // [N][FP_NLT]
+};
+int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out);
+
+// Device views of the tables (pointers into context-owned device memory).
+#include <stdint.h>
+struct DevTab {
+    const double* coef;
+    const int* src;
+    const double* lam;
+    const double* wdiag;
+};
+struct DevBlk {                      // block structure of every degree, packed
+    const int* glob;
+    const uint8_t* sb_k;
+    const uint8_t* sb_g;
+    const float* sb_cf;
+    const uint8_t* dn_k;
+    const uint8_t* dn_g;
+    const float* dn_cf;
+    const uint8_t* up_k;
+    const uint8_t* up_g;
+    const float* up_cf;
+    const uint8_t* dnT;
+    int off[FP_L_MAX + 2];           // first packed row of degree L
+};
+void fp_free_blocks(FpBlkHost* b);
 void fp_gauss_legendre(int n, double* x, double* w);

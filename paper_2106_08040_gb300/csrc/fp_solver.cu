@@ -2,42 +2,37 @@
 // Eq. convection, Eq. mean_magmom_FP) on sm_103a.
 //
 // One CTA owns one instance at a time (persistent loop over instances).  The
-// real-SH coefficient vector c (N = (L+1)^2 doubles) and every Radau stage
-// live in shared memory; nothing is streamed from HBM per step except the
-// (L1/L2-resident) closed-form coupling tables shared by all instances.
+// real-SH coefficient vector c (N = (L+1)^2 doubles), every Radau stage and
+// the FP32 factors live in shared memory; nothing is streamed from HBM per
+// step except the L1/L2-resident coupling tables shared by all instances.
 //
-// Time step: 3-stage Radau IIA (order 5, L-stable), simplified Newton:
-//   residual  R_i = -Z_i + h sum_j a_ij A(t + c_j h)(y + Z_j)        FP64
-//   correction (Lam - h_f Abar) dW = K R,  dZ = T dW (h_f / h)         FP32
-// where Abar = A(t_f + h_f) is frozen for up to refactor_every steps and the
-// block-tridiagonal (in |m|) matrices Lam - h_f Abar (one real, one complex
-// shift) are factorised in FP32 as explicit inverses of their Schur-complement
-// diagonal blocks (block Thomas; warp-level Gauss-Jordan with partial
-// pivoting).  Embedded error estimate filtered through the real factor;
-// steps land on every output sample time.
+// Time step: S-stage Radau IIA (S = 3: order 5, S = 5: order 9; L-stable),
+// simplified Newton:
+//   residual   R_i = -Z_i + h sum_j a_ij A(t + c_j h)(y + Z_j)         FP64
+//   correction (Lam - h_f Abar) dW = K R,  dZ = T dW (h_f / h)          FP32
+// Abar = A(t_f + h_f) is frozen over several steps.  Lam - h_f Abar splits into
+// one real and (S-1)/2 complex systems, each block-tridiagonal in |m|; every
+// system is factorised (block Thomas) into explicit FP32 inverses of its
+// Schur-complement diagonal blocks, one warp per system (Gauss-Jordan with
+// partial pivoting in registers), and solved by one warp per system.
+// Embedded error estimate filtered through the real factor; steps land on
+// every output sample time.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "fp_internal.h"
 
 #define NT 256
 #define NWARP (NT / 32)
-#define NLAT 12          // lateral slots SL_RX..SL_RY+1 (4) and SL_GX..SL_GY+3 (8)
 #define FULLMASK 0xffffffffu
 
-__constant__ FpRadau c_rad;
+__constant__ FpRadau c_radau[2];      // [0]: 3 stages, [1]: 5 stages
+template <int S> __device__ __forceinline__ const FpRadau& RAD() { return c_radau[S == 5 ? 1 : 0]; }
 __constant__ double c_glx[FP_NGL];
 __constant__ double c_glw[FP_NGL];
 
-struct DevTab {
-    const double* coef;
-    const int* src;
-    const int* tslot;
-    const double* lam;
-    const double* wdiag;
-};
-
 struct KArgs {
     DevTab tab;
+    DevBlk blk;
     fp_material mat;
     fp_drive drv;
     fp_tol tol;
@@ -55,89 +50,89 @@ struct KArgs {
 __host__ __device__ constexpr int grp_of(int k) {
     return k < 2 ? 0 : k < 4 ? 1 : k < 5 ? 2 : k < 7 ? 3 : k < 9 ? 4 : k < 11 ? 5 : k < 15 ? 6 : 7;
 }
-// lateral slot index (0..11) of slot k, or -1
-__host__ __device__ constexpr int lat_of(int k) {
-    return (k >= SL_RX && k < SL_GZ) ? k - SL_RX : (k >= SL_GX ? k - SL_GX + 4 : -1);
-}
-__host__ __device__ constexpr int slot_of_lat(int q) { return q < 4 ? SL_RX + q : SL_GX + (q - 4); }
 
 struct AScal { double s[8]; };
 
 // ---------------------------------------------------------------- layout ----
-struct Layout {
-    int N, L, nmax;
-    size_t y, Z, F, tmp, yb, diag, rr, rc, zr, zc, latv, fr, fc, s1r, s2r, s1c, s2c, ic, total;
-};
-
 __host__ __device__ inline int nblk(int mu, int L) { return mu == 0 ? L + 1 : 2 * (L + 1 - mu); }
-
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+struct Layout {
+    int N, L, nmax;
+    size_t y, Z, F, f0, yb, diag, rr, zr, rc, zc, dnv, upv, fr, fc, Xr, Xc, ic, total;
+    size_t fsum;
+};
+
+template <int S>
 __host__ __device__ inline Layout make_layout(int L) {
+    constexpr int NC = (S - 1) / 2;
     Layout ly;
     ly.L = L;
     ly.N = (L + 1) * (L + 1);
-    ly.nmax = L >= 1 ? (2 * L > L + 1 ? 2 * L : L + 1) : 1;
+    ly.nmax = (2 * L > L + 1) ? 2 * L : L + 1;
     size_t fsum = 0;
     for (int mu = 0; mu <= L; ++mu) fsum += (size_t)nblk(mu, L) * nblk(mu, L);
-    size_t o = 0;
+    ly.fsum = fsum;
     const size_t N = ly.N, nm2 = (size_t)ly.nmax * ly.nmax;
+    size_t o = 0;
     ly.y = o;    o = al16(o + N * 8);
-    ly.Z = o;    o = al16(o + 3 * N * 8);
-    ly.F = o;    o = al16(o + 3 * N * 8);
-    ly.tmp = o;  o = al16(o + N * 8);
+    ly.Z = o;    o = al16(o + (size_t)S * N * 8);
+    ly.F = o;    o = al16(o + (size_t)S * N * 8);
+    ly.f0 = o;   o = al16(o + N * 8);
     ly.yb = o;   o = al16(o + N * 8);
     ly.diag = o; o = al16(o + N * 8);
     ly.rr = o;   o = al16(o + N * 4);
-    ly.rc = o;   o = al16(o + N * 8);
     ly.zr = o;   o = al16(o + N * 4);
-    ly.zc = o;   o = al16(o + N * 8);
-    ly.latv = o; o = al16(o + N * NLAT * 4);
+    ly.rc = o;   o = al16(o + (size_t)NC * N * 8);
+    ly.zc = o;   o = al16(o + (size_t)NC * N * 8);
+    ly.dnv = o;  o = al16(o + N * FP_NLT * 4);
+    ly.upv = o;  o = al16(o + N * FP_NLT * 4);
     ly.fr = o;   o = al16(o + fsum * 4);
-    ly.fc = o;   o = al16(o + fsum * 8);
-    ly.s1r = o;  o = al16(o + nm2 * 4);
-    ly.s2r = o;  o = al16(o + nm2 * 4);
-    ly.s1c = o;  o = al16(o + nm2 * 8);
-    ly.s2c = o;  o = al16(o + nm2 * 8);
-    ly.ic = ly.fr;                                    // initial-state scratch aliases the factors
+    ly.fc = o;   o = al16(o + (size_t)NC * fsum * 8);
+    ly.Xr = o;   o = al16(o + nm2 * 4);
+    ly.Xc = o;   o = al16(o + (size_t)NC * nm2 * 8);
+    ly.ic = ly.fr;                                     // initial-state scratch aliases the factors
     size_t ic_end = ly.ic + (size_t)FP_NGL * (L + 1) * 8;
     ly.total = o > ic_end ? o : al16(ic_end);
     return ly;
 }
 
-size_t fp_solver_smem_bytes(int L) { return make_layout(L).total; }
-
-// ------------------------------------------------------------- helpers ----
-__device__ __forceinline__ int isqrt_i(int g) {
-    int l = (int)sqrtf((float)g + 0.5f);
-    while ((l + 1) * (l + 1) <= g) ++l;
-    while (l * l > g) --l;
-    return l;
-}
-__device__ __forceinline__ void glob_to_blk(int g, int& mu, int& k) {
-    int l = isqrt_i(g), m = g - l * l - l;
-    mu = m < 0 ? -m : m;
-    k = mu == 0 ? l : 2 * (l - mu) + (m < 0 ? 1 : 0);
-}
-__device__ __forceinline__ int blk_to_glob(int mu, int k) {
-    if (mu == 0) return k * k + k;
-    int l = mu + (k >> 1), m = (k & 1) ? -mu : mu;
-    return l * l + l + m;
+size_t fp_solver_smem_bytes(int stages, int L) {
+    return stages == 5 ? make_layout<5>(L).total : make_layout<3>(L).total;
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {   // a*b + c
+// --------------------------------------------------- scalar/complex ops ----
+__device__ __forceinline__ float cabs1(float a) { return fabsf(a); }
+__device__ __forceinline__ float cabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ __forceinline__ float cmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float cfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
     return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
-__device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cfma(float a, float2 b, float2 c) { return make_float2(fmaf(a, b.x, c.x), fmaf(a, b.y, c.y)); }
+__device__ __forceinline__ float crecip(float a) { return 1.f / a; }
+__device__ __forceinline__ float2 crecip(float2 a) {
+    float d = 1.f / (a.x * a.x + a.y * a.y);
+    return make_float2(a.x * d, -a.y * d);
+}
+__device__ __forceinline__ float cneg(float a) { return -a; }
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float cshfl(float a, int p) { return __shfl_sync(FULLMASK, a, p); }
+__device__ __forceinline__ float2 cshfl(float2 a, int p) {
+    return make_float2(__shfl_sync(FULLMASK, a.x, p), __shfl_sync(FULLMASK, a.y, p));
+}
+__device__ __forceinline__ float cadd_real(float a, float v) { return a + v; }
+__device__ __forceinline__ float2 cadd_real(float2 a, float v) { return make_float2(a.x + v, a.y); }
+template <class T> __device__ __forceinline__ T czero();
+template <> __device__ __forceinline__ float czero<float>() { return 0.f; }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 
+// ------------------------------------------------------------- helpers ----
 __device__ float block_max(float v, float* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULLMASK, v, o));
-    int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
     __syncthreads();
-    if (ln == 0) red[w] = v;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float r = red[0];
     for (int i = 1; i < NWARP; ++i) r = fmaxf(r, red[i]);
@@ -165,7 +160,7 @@ __device__ __forceinline__ AScal make_scal(const FpParams& P, const double* B) {
     return s;
 }
 
-// y = A x for rows i = tid, tid+nthr, ... (FP64, matrix-free from the tables)
+// row i of A x (FP64, matrix-free from the closed-form tables)
 __device__ __forceinline__ double apply_row(int i, const double* __restrict__ x, const AScal& sc,
                                             const double* __restrict__ diag, int N, const DevTab& T) {
     const double* cf = T.coef + (size_t)i * FP_NSLOT;
@@ -190,300 +185,235 @@ __device__ void apply_A(const double* __restrict__ x, double* __restrict__ y, co
     for (int i = threadIdx.x; i < N; i += NT) y[i] = apply_row(i, x, sc, diag, N, T);
 }
 
-// ------------------------------------------------- warp Gauss-Jordan ------
-// In-place inversion of an n x n (n <= 32) matrix S (row-major) with partial
-// pivoting; lane r holds row r in registers.  The inverse is stored
-// column-major (out[c * n + r] = Inv[r][c]) for conflict-free matvecs.
-__device__ void warp_gj_real(const float* S, float* out, int n, int* pp) {
-    const int lane = threadIdx.x & 31;
-    float a[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = (lane < n && j < n) ? S[lane * n + j] : (j == lane ? 1.f : 0.f);
-    bool used = lane >= n;
-    int myk = -1;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        if (k < n) {
-            float v = used ? 0.f : fabsf(a[k]);
-            unsigned key = (__float_as_uint(v) & ~31u) | (unsigned)lane;
-            key = __reduce_max_sync(FULLMASK, key);
-            int p = (int)(key & 31u);
-            if (lane == 0) pp[k] = p;
-            float pk = __shfl_sync(FULLMASK, a[k], p);
-            float pinv = 1.f / pk;
-            float f = a[k];
-            bool ispiv = lane == p;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j == k) continue;
-                float prj = __shfl_sync(FULLMASK, a[j], p);
-                a[j] = ispiv ? prj * pinv : fmaf(-f * pinv, prj, a[j]);
-            }
-            a[k] = ispiv ? pinv : -f * pinv;
-            if (ispiv) { used = true; myk = k; }
-        }
-    }
-    __syncwarp();
-    if (lane < n && myk >= 0 && myk < n) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j < n && pp[j] < n) out[pp[j] * n + myk] = a[j];   // pp[j] >= n only for a singular block
-    }
-    __syncwarp();
-}
-
-__device__ void warp_gj_cplx(const float2* S, float2* out, int n, int* pp) {
-    const int lane = threadIdx.x & 31;
-    float2 a[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        a[j] = (lane < n && j < n) ? S[lane * n + j] : make_float2(j == lane ? 1.f : 0.f, 0.f);
-    bool used = lane >= n;
-    int myk = -1;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        if (k < n) {
-            float v = used ? 0.f : fabsf(a[k].x) + fabsf(a[k].y);
-            unsigned key = (__float_as_uint(v) & ~31u) | (unsigned)lane;
-            key = __reduce_max_sync(FULLMASK, key);
-            int p = (int)(key & 31u);
-            if (lane == 0) pp[k] = p;
-            float2 pk = make_float2(__shfl_sync(FULLMASK, a[k].x, p), __shfl_sync(FULLMASK, a[k].y, p));
-            float d = 1.f / (pk.x * pk.x + pk.y * pk.y);
-            float2 pinv = make_float2(pk.x * d, -pk.y * d);
-            float2 f = a[k];
-            float2 fp = cmul(f, pinv);
-            bool ispiv = lane == p;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j == k) continue;
-                float2 prj = make_float2(__shfl_sync(FULLMASK, a[j].x, p), __shfl_sync(FULLMASK, a[j].y, p));
-                a[j] = ispiv ? cmul(prj, pinv) : cfma(make_float2(-fp.x, -fp.y), prj, a[j]);
-            }
-            a[k] = ispiv ? pinv : make_float2(-fp.x, -fp.y);
-            if (ispiv) { used = true; myk = k; }
-        }
-    }
-    __syncwarp();
-    if (lane < n && myk >= 0 && myk < n) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j < n && pp[j] < n) out[pp[j] * n + myk] = a[j];   // pp[j] >= n only for a singular block
-    }
-    __syncwarp();
-}
-
 // ------------------------------------------------------- per-CTA state ----
+template <int S>
 struct Ctx {
     Layout ly;
     int L, N;
-    double* y; double* Z; double* F; double* tmp; double* yb; double* diag;
-    float* rr; float2* rc; float* zr; float2* zc; float* latv;
-    float* fr; float2* fc; float* s1r; float* s2r; float2* s1c; float2* s2c;
-    int* boff; int* foff;
+    double *y, *Z, *F, *f0, *yb, *diag;
+    float *rr, *zr;
+    float2 *rc, *zc;
+    float *dnv, *upv;
+    float* fr;
+    float2* fc;
+    float* Xr;
+    float2* Xc;
+    int* boff;
+    int* foff;
+    // block structure of degree L
+    const int* glob;
+    const uint8_t *sb_k, *sb_g, *dn_k, *dn_g, *up_k, *up_g, *dnT;
+    const float *sb_cf, *dn_cf, *up_cf;
 };
 
-// latv[i][q] = entry of (shift - h Abar) at row i, lateral slot q (= -h Abar_ij)
-__device__ void build_latv(Ctx& C, const DevTab& T, const AScal& sc, double h) {
-    for (int e = threadIdx.x; e < C.N * NLAT; e += NT) {
-        int i = e / NLAT, q = e - i * NLAT, k = slot_of_lat(q);
-        int j = __ldg(T.src + (size_t)i * FP_NSLOT + k);
-        float v = 0.f;
-        if ((unsigned)j < (unsigned)C.N)
-            v = (float)(-h * sc.s[grp_of(k)] * __ldg(T.coef + (size_t)i * FP_NSLOT + k));
-        C.latv[e] = v;
+// ------------------------------------------- factorisation (block Thomas) --
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// A group of GW warps assembles the Schur-complement block
+// D~_mu = D_mu - C_mu X_{mu-1} of one system (lane = row, warp gw owns the
+// columns [gw*CPW, gw*CPW + CPW)) and inverts it in place by Gauss-Jordan with
+// partial pivoting: the warp owning pivot column k picks the pivot row and
+// publishes the column multipliers through shared memory, one named barrier
+// per pivot.  The inverse is stored column-major (out[c * n + r] = Inv[r][c]).
+// n <= 32.
+template <class T, int S, int GW>
+__device__ void group_factor_block(Ctx<S>& C, int mu, T shift, const float* gs, float h, const T* Xprev, T* out,
+                                   int* pp, T* colbuf, int gw, int barid) {
+    constexpr int CPW = 32 / GW;
+    const int lane = threadIdx.x & 31;
+    const int L = C.L, n = nblk(mu, L), bo = C.boff[mu];
+    const int j0 = gw * CPW;
+    T a[CPW];
+    if (lane < n) {
+        const int b = bo + lane;
+        const int g = __ldg(C.glob + b);
+        const T dv = cadd_real(shift, (float)(-(double)h * C.diag[g]));
+        int ks[FP_NSB];
+        float vs[FP_NSB];
+#pragma unroll
+        for (int p = 0; p < FP_NSB; ++p) {
+            ks[p] = __ldg(C.sb_k + b * FP_NSB + p);
+            vs[p] = ks[p] == 255 ? 0.f : gs[__ldg(C.sb_g + b * FP_NSB + p)] * __ldg(C.sb_cf + b * FP_NSB + p);
+        }
+        int kd[FP_NLT];
+        float vd[FP_NLT];
+#pragma unroll
+        for (int p = 0; p < FP_NLT; ++p) {
+            kd[p] = mu > 0 ? __ldg(C.dn_k + b * FP_NLT + p) : 255;
+            vd[p] = kd[p] == 255 ? 0.f : C.dnv[b * FP_NLT + p];
+        }
+#pragma unroll
+        for (int jj = 0; jj < CPW; ++jj) {
+            const int j = j0 + jj;
+            T v = j == lane ? dv : czero<T>();
+            if (j < n) {
+#pragma unroll
+                for (int p = 0; p < FP_NSB; ++p) v = cadd_real(v, ks[p] == j ? vs[p] : 0.f);
+#pragma unroll
+                for (int p = 0; p < FP_NLT; ++p)
+                    if (kd[p] != 255) v = cfma(-vd[p], Xprev[kd[p] * n + j], v);
+            }
+            a[jj] = v;
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < CPW; ++jj) a[jj] = cadd_real(czero<T>(), j0 + jj == lane ? 1.f : 0.f);
+    }
+    bool used = lane >= n;
+    int myk = -1;
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        const int owner = k / CPW, kk = k - owner * CPW;
+        T* cb = colbuf + (k & 1) * 32;
+        if (gw == owner) {
+            T ak = a[0];
+#pragma unroll
+            for (int jj = 1; jj < CPW; ++jj) ak = jj == kk ? a[jj] : ak;
+            const float v = used ? 0.f : cabs1(ak);
+            unsigned key = (__float_as_uint(v) & ~31u) | (unsigned)lane;
+            key = __reduce_max_sync(FULLMASK, key);
+            const int p = (int)(key & 31u);
+            const T pinv = crecip(cshfl(ak, p));
+            cb[lane] = lane == p ? pinv : cneg(cmul(ak, pinv));
+            if (lane == 0) pp[k] = p;
+        }
+        named_bar(barid, 32 * GW);
+        const int p = pp[k];
+        const T mlt = cb[lane];                 // pinv on the pivot row, -a_ik / a_pk elsewhere
+        const bool ispiv = lane == p;
+#pragma unroll
+        for (int jj = 0; jj < CPW; ++jj) {
+            const T prj = cshfl(a[jj], p);
+            const T upd = ispiv ? cmul(prj, mlt) : cfma(mlt, prj, a[jj]);
+            a[jj] = (j0 + jj == k) ? mlt : upd;
+        }
+        if (ispiv) { used = true; myk = k; }
+    }
+    if (lane < n && myk >= 0) {
+#pragma unroll
+        for (int jj = 0; jj < CPW; ++jj) {
+            const int j = j0 + jj;
+            if (j < n) {
+                const int pj = pp[j];
+                if (pj < n) out[pj * n + myk] = a[jj];       // pj >= n only for a singular block
+            }
+        }
     }
 }
 
-// Factorise (gam - h Abar) [real] and ((alp - i bet) - h Abar) [complex].
-__device__ void factorize(Ctx& C, const DevTab& T, const AScal& sc, double h, int* pp) {
+// X_mu = Inv_mu B_mu (n x n2, row-major) for one system; one warp per column c
+// (lane = row r).  B_mu[k][c] is the coupling of row k (block mu) to row c
+// (block mu+1), reached through the dn list of row c and its back pointer.
+template <class T, int S>
+__device__ __forceinline__ void x_column(Ctx<S>& C, int mu, int c, const T* inv, T* X) {
+    const int lane = threadIdx.x & 31;
+    const int L = C.L, n = nblk(mu, L), n2 = nblk(mu + 1, L);
+    const int bc = C.boff[mu + 1] + c, bo = C.boff[mu];
+    T acc = czero<T>();
+#pragma unroll
+    for (int p = 0; p < FP_NLT; ++p) {
+        const int k = __ldg(C.dn_k + bc * FP_NLT + p);
+        if (k == 255) continue;
+        const int q = __ldg(C.dnT + bc * FP_NLT + p);
+        const float bv = q == 255 ? 0.f : C.upv[(bo + k) * FP_NLT + q];
+        if (lane < n) acc = cfma(bv, inv[k * n + lane], acc);
+    }
+    if (lane < n) X[lane * n2 + c] = acc;
+}
+
+template <int S>
+__device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2* colbuf) {
+    constexpr int NC = (S - 1) / 2;
+    constexpr int NSYS = 1 + NC;
+    constexpr int GW = NWARP / NSYS >= 4 ? 4 : (NWARP / NSYS >= 2 ? 2 : 1);
     const int L = C.L, N = C.N;
-    const float gam = (float)c_rad.gam, alp = (float)c_rad.alp, bet = (float)c_rad.bet;
-    build_latv(C, T, sc, h);
+    float gs[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) gs[q] = (float)(-h * sc.s[q]);
+    for (int e = threadIdx.x; e < N * FP_NLT; e += NT) {
+        int kd = __ldg(C.dn_k + e), ku = __ldg(C.up_k + e);
+        C.dnv[e] = kd == 255 ? 0.f : gs[__ldg(C.dn_g + e)] * __ldg(C.dn_cf + e);
+        C.upv[e] = ku == 255 ? 0.f : gs[__ldg(C.up_g + e)] * __ldg(C.up_cf + e);
+    }
     __syncthreads();
+    const int w = threadIdx.x >> 5;
+    const int sys = w / GW, gw = w - sys * GW;
+    const size_t nm2 = (size_t)C.ly.nmax * C.ly.nmax;
     for (int mu = 0; mu <= L; ++mu) {
-        const int n = nblk(mu, L);
-        // (1) diagonal block D_mu of the shifted matrix
-        for (int e = threadIdx.x; e < n * n; e += NT) { C.s1r[e] = 0.f; C.s1c[e] = make_float2(0.f, 0.f); }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += NT) {
-            int g = blk_to_glob(mu, r);
-            float vd = (float)(-h * C.diag[g]);
-            C.s1r[r * n + r] += gam + vd;
-            C.s1c[r * n + r] = make_float2(C.s1c[r * n + r].x + alp + vd, C.s1c[r * n + r].y - bet);
-            const double* cf = T.coef + (size_t)g * FP_NSLOT;
-            const int* sr = T.src + (size_t)g * FP_NSLOT;
-#pragma unroll
-            for (int k = 0; k < SL_RX; ++k) {                       // W, ZR, RZ: same |m|
-                int j = __ldg(sr + k);
-                if ((unsigned)j >= (unsigned)N) continue;
-                int mj, kj;
-                glob_to_blk(j, mj, kj);
-                float v = (float)(-h * sc.s[grp_of(k)] * __ldg(cf + k));
-                C.s1r[r * n + kj] += v;
-                C.s1c[r * n + kj].x += v;
-            }
-#pragma unroll
-            for (int k = SL_GZ; k < SL_GX; ++k) {                   // GZ: same |m|
-                int j = __ldg(sr + k);
-                if ((unsigned)j >= (unsigned)N) continue;
-                int mj, kj;
-                glob_to_blk(j, mj, kj);
-                float v = (float)(-h * sc.s[grp_of(k)] * __ldg(cf + k));
-                C.s1r[r * n + kj] += v;
-                C.s1c[r * n + kj].x += v;
-            }
+        if (sys == 0) {
+            group_factor_block<float, S, GW>(C, mu, (float)RAD<S>().gam, gs, (float)h, C.Xr, C.fr + C.foff[mu],
+                                             pp, (float*)colbuf, gw, 1);
+        } else if (sys <= NC) {
+            const int q = sys - 1;
+            const float2 shift = make_float2((float)RAD<S>().alp[q], -(float)RAD<S>().bet[q]);
+            group_factor_block<float2, S, GW>(C, mu, shift, gs, (float)h, C.Xc + q * nm2,
+                                              C.fc + (size_t)q * C.ly.fsum + C.foff[mu], pp + 32 * sys,
+                                              colbuf + 64 * sys, gw, 1 + sys);
         }
         __syncthreads();
-        // Schur complement: D~ = D - C_mu X_{mu-1},  X_{mu-1} = Inv_{mu-1} B_{mu-1} in s2
-        if (mu > 0) {
-            const int np = nblk(mu - 1, L);
-            for (int e = threadIdx.x; e < n * n; e += NT) {
-                int r = e / n, c = e - r * n;
-                int g = blk_to_glob(mu, r);
-                float ar = 0.f;
-                float2 ac = make_float2(0.f, 0.f);
-                for (int q = 0; q < NLAT; ++q) {
-                    int j = __ldg(T.src + (size_t)g * FP_NSLOT + slot_of_lat(q));
-                    if ((unsigned)j >= (unsigned)N) continue;
-                    int mj, kj;
-                    glob_to_blk(j, mj, kj);
-                    if (mj != mu - 1) continue;
-                    float v = C.latv[g * NLAT + q];
-                    ar = fmaf(v, C.s2r[kj * n + c], ar);
-                    ac.x = fmaf(v, C.s2c[kj * n + c].x, ac.x);
-                    ac.y = fmaf(v, C.s2c[kj * n + c].y, ac.y);
-                }
-                C.s1r[e] -= ar;
-                C.s1c[e].x -= ac.x;
-                C.s1c[e].y -= ac.y;
-            }
-            (void)np;
-            __syncthreads();
-        }
-        // (2) invert the two diagonal blocks, one warp each
-        const int w = threadIdx.x >> 5;
-        if (w == 0) warp_gj_real(C.s1r, C.fr + C.foff[mu], n, pp);
-        else if (w == 1) warp_gj_cplx(C.s1c, C.fc + C.foff[mu], n, pp + 32);
-        __syncthreads();
-        // (3) X_mu = Inv_mu B_mu (n x n2) for the next block
         if (mu < L) {
             const int n2 = nblk(mu + 1, L);
-            const float* Ir = C.fr + C.foff[mu];
-            const float2* Ic = C.fc + C.foff[mu];
-            for (int e = threadIdx.x; e < n * n2; e += NT) {
-                int r = e / n2, c = e - r * n2;
-                int gc = blk_to_glob(mu + 1, c);
-                float ar = 0.f;
-                float2 ac = make_float2(0.f, 0.f);
-                for (int q = 0; q < NLAT; ++q) {
-                    int s = slot_of_lat(q);
-                    int j = __ldg(T.src + (size_t)gc * FP_NSLOT + s);
-                    if ((unsigned)j >= (unsigned)N) continue;
-                    int mj, kj;
-                    glob_to_blk(j, mj, kj);
-                    if (mj != mu) continue;
-                    int t = __ldg(T.tslot + (size_t)gc * FP_NSLOT + s);
-                    // B_mu[kj][c]; no back-slot means a structurally zero entry
-                    // (row (0,0) of A vanishes: conservation of mass)
-                    float bval = t >= 0 ? C.latv[j * NLAT + lat_of(t)] : 0.f;
-                    ar = fmaf(Ir[kj * n + r], bval, ar);            // Inv[r][kj]
-                    ac = cfma(Ic[kj * n + r], make_float2(bval, 0.f), ac);
-                }
-                C.s2r[r * n2 + c] = ar;
-                C.s2c[r * n2 + c] = ac;
+            for (int item = w; item < NSYS * n2; item += NWARP) {
+                const int sy = item / n2, c = item - sy * n2;
+                if (sy == 0) x_column<float, S>(C, mu, c, C.fr + C.foff[mu], C.Xr);
+                else x_column<float2, S>(C, mu, c, C.fc + (size_t)(sy - 1) * C.ly.fsum + C.foff[mu],
+                                         C.Xc + (sy - 1) * nm2);
             }
             __syncthreads();
         }
     }
 }
 
-// Block-Thomas solve with the explicit block inverses; rr/rc hold the right-hand
-// sides in block order, the solutions end in zr/zc.  Real rows run on warps
-// 0-3, complex rows on warps 4-7.
-__device__ void solve_blocks(Ctx& C, const DevTab& T, bool do_cplx) {
-    const int L = C.L, N = C.N;
-    const int half = NT / 2;
-    const bool is_c = threadIdx.x >= half;
-    const int tl = is_c ? threadIdx.x - half : threadIdx.x;
-    if (is_c && !do_cplx) {
-        // still take part in every barrier below
-    }
+// ------------------------------------------------------ warp-level solve --
+// Block-Thomas solve of one system with its explicit block inverses: rhs (block
+// order) is overwritten, the solution ends in z.  Called by one full warp.
+template <class T, int S>
+__device__ void warp_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z) {
+    const int lane = threadIdx.x & 31;
+    const int L = C.L;
     for (int mu = 0; mu <= L; ++mu) {
-        const int n = nblk(mu, L), bo = C.boff[mu];
-        if (mu > 0) {
-            const int bp = C.boff[mu - 1];
-            for (int r = tl; r < n; r += half) {
-                if (is_c && !do_cplx) break;
-                int g = blk_to_glob(mu, r);
-                float ar = 0.f;
-                float2 ac = make_float2(0.f, 0.f);
-                for (int q = 0; q < NLAT; ++q) {
-                    int j = __ldg(T.src + (size_t)g * FP_NSLOT + slot_of_lat(q));
-                    if ((unsigned)j >= (unsigned)N) continue;
-                    int mj, kj;
-                    glob_to_blk(j, mj, kj);
-                    if (mj != mu - 1) continue;
-                    float v = C.latv[g * NLAT + q];
-                    if (is_c) ac = cfma(make_float2(v, 0.f), C.zc[bp + kj], ac);
-                    else ar = fmaf(v, C.zr[bp + kj], ar);
-                }
-                if (is_c) { C.rc[bo + r].x -= ac.x; C.rc[bo + r].y -= ac.y; }
-                else C.rr[bo + r] -= ar;
+        const int n = nblk(mu, L), bo = C.boff[mu], fo = C.foff[mu];
+        if (lane < n && mu > 0) {
+            const int b = bo + lane, bp = C.boff[mu - 1];
+            T v = rhs[b];
+#pragma unroll
+            for (int p = 0; p < FP_NLT; ++p) {
+                int k = __ldg(C.dn_k + b * FP_NLT + p);
+                if (k != 255) v = cfma(-C.dnv[b * FP_NLT + p], z[bp + k], v);
             }
-            __syncthreads();
+            rhs[b] = v;
         }
-        const int fo = C.foff[mu];
-        for (int r = tl; r < n; r += half) {
-            if (is_c && !do_cplx) break;
-            if (is_c) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int c = 0; c < n; ++c) acc = cfma(C.fc[fo + c * n + r], C.rc[bo + c], acc);
-                C.zc[bo + r] = acc;
-            } else {
-                float acc = 0.f;
-                for (int c = 0; c < n; ++c) acc = fmaf(C.fr[fo + c * n + r], C.rr[bo + c], acc);
-                C.zr[bo + r] = acc;
-            }
+        __syncwarp();
+        if (lane < n) {
+            T acc = czero<T>();
+#pragma unroll 8
+            for (int c = 0; c < n; ++c) acc = cfma(inv[fo + c * n + lane], rhs[bo + c], acc);
+            z[bo + lane] = acc;
         }
-        __syncthreads();
+        __syncwarp();
     }
     for (int mu = L - 1; mu >= 0; --mu) {
-        const int n = nblk(mu, L), bo = C.boff[mu], bn = C.boff[mu + 1];
-        for (int r = tl; r < n; r += half) {
-            if (is_c && !do_cplx) break;
-            int g = blk_to_glob(mu, r);
-            float ar = 0.f;
-            float2 ac = make_float2(0.f, 0.f);
-            for (int q = 0; q < NLAT; ++q) {
-                int j = __ldg(T.src + (size_t)g * FP_NSLOT + slot_of_lat(q));
-                if ((unsigned)j >= (unsigned)N) continue;
-                int mj, kj;
-                glob_to_blk(j, mj, kj);
-                if (mj != mu + 1) continue;
-                float v = C.latv[g * NLAT + q];
-                if (is_c) ac = cfma(make_float2(v, 0.f), C.zc[bn + kj], ac);
-                else ar = fmaf(v, C.zr[bn + kj], ar);
+        const int n = nblk(mu, L), bo = C.boff[mu], fo = C.foff[mu], bn = C.boff[mu + 1];
+        if (lane < n) {
+            const int b = bo + lane;
+            T v = czero<T>();
+#pragma unroll
+            for (int p = 0; p < FP_NLT; ++p) {
+                int k = __ldg(C.up_k + b * FP_NLT + p);
+                if (k != 255) v = cfma(C.upv[b * FP_NLT + p], z[bn + k], v);
             }
-            if (is_c) C.rc[bo + r] = ac;
-            else C.rr[bo + r] = ar;
+            rhs[b] = v;
         }
-        __syncthreads();
-        const int fo = C.foff[mu];
-        for (int r = tl; r < n; r += half) {
-            if (is_c && !do_cplx) break;
-            if (is_c) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int c = 0; c < n; ++c) acc = cfma(C.fc[fo + c * n + r], C.rc[bo + c], acc);
-                C.zc[bo + r].x -= acc.x;
-                C.zc[bo + r].y -= acc.y;
-            } else {
-                float acc = 0.f;
-                for (int c = 0; c < n; ++c) acc = fmaf(C.fr[fo + c * n + r], C.rr[bo + c], acc);
-                C.zr[bo + r] -= acc;
-            }
+        __syncwarp();
+        if (lane < n) {
+            T acc = czero<T>();
+#pragma unroll 8
+            for (int c = 0; c < n; ++c) acc = cfma(inv[fo + c * n + lane], rhs[bo + c], acc);
+            z[bo + lane] = cfma(-1.f, acc, z[bo + lane]);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -491,10 +421,13 @@ __device__ void solve_blocks(Ctx& C, const DevTab& T, bool do_cplx) {
 // Projection of the Boltzmann density f ~ exp(bT B.m + sigma z^2) (easy-axis
 // frame) on the real SH basis.  The azimuthal integral is exact through the
 // modified Bessel functions: int exp(k cos(p - pB)) cos(mu p) dp = 2 pi I_mu(k) cos(mu pB);
-// the polar integral uses FP_NGL Gauss-Legendre nodes.
-__device__ void initial_state(Ctx& C, const FpParams& P, const double* B) {
+// the polar integral uses FP_NGL Gauss-Legendre nodes.  I_mu(k) e^{-k} by the
+// backward ratio recurrence r_mu = k / (2 mu + k r_{mu+1}) normalised with
+// e^k = I_0 + 2 sum_mu I_mu.
+template <int S>
+__device__ void initial_state(Ctx<S>& C, const FpParams& P, const double* B, unsigned char* smem) {
     const int L = C.L;
-    double* E = (double*)((char*)C.y - C.ly.y + C.ly.ic);   // [FP_NGL][L+1]
+    double* E = (double*)(smem + C.ly.ic);   // [FP_NGL][L+1]
     const double pi = 3.14159265358979323846;
     double Bp = sqrt(B[0] * B[0] + B[1] * B[1]);
     double Babs = sqrt(Bp * Bp + B[2] * B[2]);
@@ -533,16 +466,17 @@ __device__ void initial_state(Ctx& C, const FpParams& P, const double* B) {
         double cphi = cos(mu * phiB), sphi = sin(mu * phiB);
         for (int l = mu; l <= L; ++l) {
             double part = 0.0;
+            double a = 0.0, b = 0.0;
+            if (l >= mu + 2) {
+                a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)mu * mu));
+                b = sqrt((((double)l - 1.0) * (l - 1.0) - (double)mu * mu) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+            }
 #pragma unroll
             for (int q = 0; q < FP_NGL / 32; ++q) {
                 double cur;
                 if (l == mu) cur = q2[q];
                 else if (l == mu + 1) cur = sqrt(2.0 * mu + 3.0) * xs[q] * q2[q];
-                else {
-                    double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)mu * mu));
-                    double b = sqrt((((double)l - 1.0) * (l - 1.0) - (double)mu * mu) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
-                    cur = a * (xs[q] * q2[q] - b * q1[q]);
-                }
+                else cur = a * (xs[q] * q2[q] - b * q1[q]);
                 if (l > mu) { q1[q] = q2[q]; q2[q] = cur; }
                 part += cur * ev[q];
             }
@@ -566,36 +500,39 @@ __device__ __forceinline__ double sample_time(const fp_drive& d, int j) {
     return ((double)d.warmup_periods + (double)j / (double)d.samples_per_period) * d.period;
 }
 
+template <int S>
 __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
+    constexpr int NC = (S - 1) / 2;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_boff[FP_L_MAX + 2], s_foff[FP_L_MAX + 2];
-    __shared__ int s_pp[64];
+    __shared__ int s_pp[32 * (1 + NC)];
+    __shared__ float2 s_colbuf[64 * (1 + NC)];
     __shared__ float s_red[NWARP];
     __shared__ double s_R[9], s_off[3], s_dm[3];
 
-    Ctx C;
-    C.ly = make_layout(A.L_launch);
+    Ctx<S> C;
+    C.ly = make_layout<S>(A.L_launch);
     C.y = (double*)(smem + C.ly.y);
     C.Z = (double*)(smem + C.ly.Z);
     C.F = (double*)(smem + C.ly.F);
-    C.tmp = (double*)(smem + C.ly.tmp);
+    C.f0 = (double*)(smem + C.ly.f0);
     C.yb = (double*)(smem + C.ly.yb);
     C.diag = (double*)(smem + C.ly.diag);
     C.rr = (float*)(smem + C.ly.rr);
-    C.rc = (float2*)(smem + C.ly.rc);
     C.zr = (float*)(smem + C.ly.zr);
+    C.rc = (float2*)(smem + C.ly.rc);
     C.zc = (float2*)(smem + C.ly.zc);
-    C.latv = (float*)(smem + C.ly.latv);
+    C.dnv = (float*)(smem + C.ly.dnv);
+    C.upv = (float*)(smem + C.ly.upv);
     C.fr = (float*)(smem + C.ly.fr);
     C.fc = (float2*)(smem + C.ly.fc);
-    C.s1r = (float*)(smem + C.ly.s1r);
-    C.s2r = (float*)(smem + C.ly.s2r);
-    C.s1c = (float2*)(smem + C.ly.s1c);
-    C.s2c = (float2*)(smem + C.ly.s2c);
+    C.Xr = (float*)(smem + C.ly.Xr);
+    C.Xc = (float2*)(smem + C.ly.Xc);
     C.boff = s_boff;
     C.foff = s_foff;
     const DevTab& T = A.tab;
     const double sq43 = sqrt(4.0 * 3.14159265358979323846 / 3.0);
+    const int w = threadIdx.x >> 5;
 
     for (int inst = blockIdx.x; inst < A.n; inst += gridDim.x) {
         const fp_instance in = A.inst[inst];
@@ -615,6 +552,20 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
         C.L = L;
         C.N = (L + 1) * (L + 1);
         const int N = C.N;
+        {
+            const int o = A.blk.off[L];
+            C.glob = A.blk.glob + o;
+            C.sb_k = A.blk.sb_k + (size_t)o * FP_NSB;
+            C.sb_g = A.blk.sb_g + (size_t)o * FP_NSB;
+            C.sb_cf = A.blk.sb_cf + (size_t)o * FP_NSB;
+            C.dn_k = A.blk.dn_k + (size_t)o * FP_NLT;
+            C.dn_g = A.blk.dn_g + (size_t)o * FP_NLT;
+            C.dn_cf = A.blk.dn_cf + (size_t)o * FP_NLT;
+            C.up_k = A.blk.up_k + (size_t)o * FP_NLT;
+            C.up_g = A.blk.up_g + (size_t)o * FP_NLT;
+            C.up_cf = A.blk.up_cf + (size_t)o * FP_NLT;
+            C.dnT = A.blk.dnT + (size_t)o * FP_NLT;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             int bo = 0, fo = 0;
@@ -635,24 +586,25 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
 
         double B[3];
         field_nframe(A, R, off, 0.0, B);
-        initial_state(C, P, B);
+        initial_state<S>(C, P, B, smem);
 
         const double T_s = A.drv.period / A.drv.samples_per_period;     // sample spacing = h_max
         const double rtol = A.tol.rtol, atol = A.tol.atol;
+        const float kappa = 0.02f;
         double t = 0.0;
-        double tau = 0.5 / P.D;
-        double h = fmin(T_s, 0.01 * tau);
+        double h = fmin(T_s, 0.01 * (0.5 / P.D));
         int jn = 0, nsteps = 0, nrej = 0, nit = 0, nfac = 0, status = FP_STATUS_OK;
         bool have_pred = false, fac_valid = false, force_refac = false;
         int since_fac = 0;
         double h_f = 0.0, h_old = 0.0;
+        float eta = 1.0f;
 
         AScal sc0 = make_scal(P, B);
-        apply_A(C.y, C.tmp, sc0, C.diag, N, T);            // f0 = A(t) y, kept in tmp
+        apply_A(C.y, C.f0, sc0, C.diag, N, T);            // f0 = A(t) y
         __syncthreads();
 
         auto write_sample = [&](int j, double tj) {
-            // <m> and d<m>/dt at t_j, rotated back to the lab frame
+            // <m> and d<m>/dt at t_j (l = 1 rows of A(t_j) y), rotated back to the lab frame
             if (threadIdx.x < 3) {
                 double Bs[3];
                 field_nframe(A, R, off, tj, Bs);
@@ -677,11 +629,9 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
 
         if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, 0.0); jn = 1; }
 
-        // |y|_inf for the error scale
         float ym = 0.f;
         for (int i = threadIdx.x; i < N; i += NT) ym = fmaxf(ym, fabsf((float)C.y[i]));
         double ymax = block_max(ym, s_red);
-        AScal scf;
 
         while (jn < A.S_out) {
             if (nsteps + nrej >= A.tol.max_steps) { status = FP_STATUS_MAXSTEPS; break; }
@@ -690,130 +640,167 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             double hs = fmin(h, T_s);
             bool last = false;
             if (t + hs >= tt - 1e-12 * T_s) { hs = tt - t; last = true; }
-            // (re)factorise the iteration matrices
-            double rat = fac_valid ? hs / h_f : 0.0;
+            const double rat = fac_valid ? hs / h_f : 0.0;
             if (!fac_valid || force_refac || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
                 double Bf[3];
                 field_nframe(A, R, off, t + hs, Bf);
-                scf = make_scal(P, Bf);
-                factorize(C, T, scf, hs, s_pp);
+                factorize<S>(C, make_scal(P, Bf), hs, s_pp, s_colbuf);
                 h_f = hs; fac_valid = true; force_refac = false; since_fac = 0; ++nfac;
             }
-            AScal scj[3];
-            for (int j = 0; j < 3; ++j) {
+            AScal scj[S];
+            for (int j = 0; j < S; ++j) {
                 double Bj[3];
-                field_nframe(A, R, off, t + c_rad.c[j] * hs, Bj);
+                field_nframe(A, R, off, t + RAD<S>().c[j] * hs, Bj);
                 scj[j] = make_scal(P, Bj);
             }
-            // predictor from the previous collocation polynomial
+            // predictor from the previous collocation polynomial (nodes 0, c_1..c_S)
             if (have_pred) {
                 const double r = hs / h_old;
-                double nd[4] = {0.0, c_rad.c[0], c_rad.c[1], c_rad.c[2]};
-                double Pm[3][3];
-                for (int i = 0; i < 3; ++i) {
-                    double tau_i = 1.0 + c_rad.c[i] * r;
-                    for (int j = 1; j < 4; ++j) {
-                        double lj = 1.0;
-                        for (int k = 0; k < 4; ++k)
-                            if (k != j) lj *= (tau_i - nd[k]) / (nd[j] - nd[k]);
-                        Pm[i][j - 1] = lj - (j == 3 ? 1.0 : 0.0);
+                double Pm[S][S];
+                for (int i = 0; i < S; ++i) {
+                    const double tau_i = 1.0 + RAD<S>().c[i] * r;
+                    for (int j = 0; j < S; ++j) {
+                        const double nj = RAD<S>().c[j];
+                        double lj = tau_i / nj;
+                        for (int k = 0; k < S; ++k)
+                            if (k != j) lj *= (tau_i - RAD<S>().c[k]) / (nj - RAD<S>().c[k]);
+                        Pm[i][j] = lj - (j == S - 1 ? 1.0 : 0.0);
                     }
                 }
                 for (int i = threadIdx.x; i < N; i += NT) {
-                    double z0 = C.Z[i], z1 = C.Z[N + i], z2 = C.Z[2 * N + i];
-                    for (int k = 0; k < 3; ++k) C.Z[k * N + i] = Pm[k][0] * z0 + Pm[k][1] * z1 + Pm[k][2] * z2;
+                    double zo[S];
+#pragma unroll
+                    for (int j = 0; j < S; ++j) zo[j] = C.Z[j * N + i];
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        double v = 0.0;
+#pragma unroll
+                        for (int j = 0; j < S; ++j) v = fma(Pm[k][j], zo[j], v);
+                        C.Z[k * N + i] = v;
+                    }
                 }
             } else {
-                for (int i = threadIdx.x; i < 3 * N; i += NT) C.Z[i] = 0.0;
+                for (int i = threadIdx.x; i < S * N; i += NT) C.Z[i] = 0.0;
             }
+            __syncthreads();
             const double sc_err = atol + rtol * ymax;
             const float fscale = (float)(h_f / hs);
             bool conv = false, nonfinite = false;
-            float prev = 3.0e38f;
+            float prev = 3.0e38f, theta = 0.f;
+            eta = powf(fmaxf(eta, 1e-7f), 0.8f);
             for (int it = 0; it < A.tol.newton_max_iter; ++it) {
                 // F_j = A(t + c_j h)(y + Z_j), FP64
-                for (int j = 0; j < 3; ++j) {
+                for (int j = 0; j < S; ++j) {
                     for (int i = threadIdx.x; i < N; i += NT) C.yb[i] = C.y[i] + C.Z[j * N + i];
                     __syncthreads();
                     apply_A(C.yb, C.F + j * N, scj[j], C.diag, N, T);
                     __syncthreads();
                 }
-                // residual and right-hand sides (block order)
-                for (int i = threadIdx.x; i < N; i += NT) {
-                    double f0v = C.F[i], f1v = C.F[N + i], f2v = C.F[2 * N + i];
-                    float Rk[3];
-                    for (int k = 0; k < 3; ++k) {
-                        double Rv = -C.Z[k * N + i] + hs * (c_rad.a[k][0] * f0v + c_rad.a[k][1] * f1v + c_rad.a[k][2] * f2v);
-                        Rk[k] = (float)Rv;
+                // residual R = -Z + h a F (FP64) -> right-hand sides K R (FP32, block order)
+                for (int b = threadIdx.x; b < N; b += NT) {
+                    const int i = __ldg(C.glob + b);
+                    double fv[S];
+                    float Rk[S];
+#pragma unroll
+                    for (int j = 0; j < S; ++j) fv[j] = C.F[j * N + i];
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        double acc = 0.0;
+#pragma unroll
+                        for (int j = 0; j < S; ++j) acc = fma(RAD<S>().a[k][j], fv[j], acc);
+                        Rk[k] = (float)fma(hs, acc, -C.Z[k * N + i]);
                     }
-                    int mu, kk;
-                    glob_to_blk(i, mu, kk);
-                    int b = C.boff[mu] + kk;
-                    float q0 = (float)c_rad.K[0][0] * Rk[0] + (float)c_rad.K[0][1] * Rk[1] + (float)c_rad.K[0][2] * Rk[2];
-                    float q1 = (float)c_rad.K[1][0] * Rk[0] + (float)c_rad.K[1][1] * Rk[1] + (float)c_rad.K[1][2] * Rk[2];
-                    float q2 = (float)c_rad.K[2][0] * Rk[0] + (float)c_rad.K[2][1] * Rk[1] + (float)c_rad.K[2][2] * Rk[2];
-                    C.rr[b] = q0;
-                    C.rc[b] = make_float2(q1, q2);
+                    float q[S];
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int j = 0; j < S; ++j) acc = fmaf((float)RAD<S>().K[k][j], Rk[j], acc);
+                        q[k] = acc;
+                    }
+                    C.rr[b] = q[0];
+#pragma unroll
+                    for (int p = 0; p < NC; ++p) C.rc[p * N + b] = make_float2(q[1 + 2 * p], q[2 + 2 * p]);
                 }
                 __syncthreads();
-                solve_blocks(C, T, true);
+                if (w == 0) warp_solve<float, S>(C, C.fr, C.rr, C.zr);
+                else if (w <= NC)
+                    warp_solve<float2, S>(C, C.fc + (size_t)(w - 1) * C.ly.fsum, C.rc + (w - 1) * N, C.zc + (w - 1) * N);
+                __syncthreads();
                 // Z += T dW (h_f / h)
                 float dm = 0.f;
-                for (int i = threadIdx.x; i < N; i += NT) {
-                    int mu, kk;
-                    glob_to_blk(i, mu, kk);
-                    int b = C.boff[mu] + kk;
-                    float w0 = fscale * C.zr[b], w1 = fscale * C.zc[b].x, w2 = fscale * C.zc[b].y;
-                    for (int k = 0; k < 3; ++k) {
-                        float dz = (float)c_rad.T[k][0] * w0 + (float)c_rad.T[k][1] * w1 + (float)c_rad.T[k][2] * w2;
+                for (int b = threadIdx.x; b < N; b += NT) {
+                    const int i = __ldg(C.glob + b);
+                    float dW[S];
+                    dW[0] = fscale * C.zr[b];
+#pragma unroll
+                    for (int p = 0; p < NC; ++p) {
+                        float2 v = C.zc[p * N + b];
+                        dW[1 + 2 * p] = fscale * v.x;
+                        dW[2 + 2 * p] = fscale * v.y;
+                    }
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        float dz = 0.f;
+#pragma unroll
+                        for (int j = 0; j < S; ++j) dz = fmaf((float)RAD<S>().T[k][j], dW[j], dz);
                         C.Z[k * N + i] += (double)dz;
                         dm = fmaxf(dm, fabsf(dz));
                     }
                 }
-                float dmax = block_max(dm, s_red);
+                const float dmax = block_max(dm, s_red);
                 ++nit;
                 if (!(dmax < 3.0e38f)) { nonfinite = true; break; }
-                if (dmax <= 0.01f * (float)sc_err) { conv = true; break; }
-                if (it >= 1 && dmax > 0.99f * prev) break;
+                if (it >= 1) {
+                    theta = dmax / prev;
+                    if (theta >= 0.99f) break;
+                    eta = theta / (1.f - theta);
+                }
+                if (eta * dmax <= kappa * (float)sc_err || dmax <= 1e-3f * (float)sc_err) { conv = true; break; }
                 prev = dmax;
             }
             if (nonfinite) { status = FP_STATUS_NONFINITE; break; }
             if (!conv) {
                 ++nrej;
-                if (since_fac == 0 && h_f == hs && hs <= 1e-6 * T_s) { status = FP_STATUS_NEWTON_FAIL; break; }
-                h = hs * 0.5; have_pred = false; force_refac = true;
+                if (since_fac == 0 && hs <= 1e-6 * T_s) { status = FP_STATUS_NEWTON_FAIL; break; }
+                if (since_fac == 0) h = hs * 0.5;      // fresh factors did not converge: shrink the step
+                have_pred = false; force_refac = true; eta = 1.0f;
                 __syncthreads();
                 continue;
             }
+            if (theta > 0.1f) force_refac = true;       // slow contraction: refresh the factors next step
             // embedded error estimate, filtered through the real factor
-            for (int i = threadIdx.x; i < N; i += NT) {
-                double ev = hs * c_rad.g0 * C.tmp[i] + c_rad.e[0] * C.Z[i] + c_rad.e[1] * C.Z[N + i] + c_rad.e[2] * C.Z[2 * N + i];
-                int mu, kk;
-                glob_to_blk(i, mu, kk);
-                C.rr[C.boff[mu] + kk] = (float)ev;
+            for (int b = threadIdx.x; b < N; b += NT) {
+                const int i = __ldg(C.glob + b);
+                double ev = hs * RAD<S>().g0 * C.f0[i];
+#pragma unroll
+                for (int j = 0; j < S; ++j) ev = fma(RAD<S>().e[j], C.Z[j * N + i], ev);
+                C.rr[b] = (float)ev;
             }
             __syncthreads();
-            solve_blocks(C, T, false);
+            if (w == 0) warp_solve<float, S>(C, C.fr, C.rr, C.zr);
+            __syncthreads();
             float em = 0.f;
-            const float escale = (float)(c_rad.gam * h_f / hs);
-            for (int i = threadIdx.x; i < N; i += NT) {
-                int mu, kk;
-                glob_to_blk(i, mu, kk);
-                em = fmaxf(em, fabsf(escale * C.zr[C.boff[mu] + kk]));
-            }
-            double en = (double)block_max(em, s_red) / sc_err;
+            const float escale = (float)(RAD<S>().gam * h_f / hs);
+            for (int b = threadIdx.x; b < N; b += NT) em = fmaxf(em, fabsf(escale * C.zr[b]));
+            const double en = (double)block_max(em, s_red) / sc_err;
             if (!(en < 1e300)) { status = FP_STATUS_NONFINITE; break; }
-            double fac = en > 0.0 ? 0.9 * pow(en, -0.25) : 4.0;
+            const double fac = en > 0.0 ? 0.9 * pow(en, -1.0 / (S + 1)) : 4.0;
             if (en <= 1.0) {
                 float ymx = 0.f;
                 for (int i = threadIdx.x; i < N; i += NT) {
-                    C.y[i] += C.Z[2 * N + i];
-                    C.tmp[i] = C.F[2 * N + i];          // f0 of the next step ~ A(t+h) y_new
+                    C.y[i] += C.Z[(S - 1) * N + i];
                     ymx = fmaxf(ymx, fabsf((float)C.y[i]));
                 }
                 ymax = block_max(ymx, s_red);
                 ++nsteps; ++since_fac;
                 t = last ? tt : t + hs;
+                {   // f0 = A(t) y at the accepted point, for the next error estimate
+                    double Bn[3];
+                    field_nframe(A, R, off, t, Bn);
+                    apply_A(C.y, C.f0, make_scal(P, Bn), C.diag, N, T);
+                    __syncthreads();
+                }
                 if (last) { write_sample(jn, tt); ++jn; }
                 double hn = hs * fmin(4.0, fmax(0.2, fac));
                 if (last && hs < h) hn = fac < 1.0 ? fmin(h, hn) : h;
@@ -834,7 +821,6 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                 A.stats[inst * 4 + 2] = nit;    A.stats[inst * 4 + 3] = nfac;
             }
         }
-        // zero the samples that were not reached
         for (int e = jn * 3 + threadIdx.x; e < A.S_out * 3; e += NT) {
             if (A.m_out) A.m_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
             if (A.dmdt_out) A.dmdt_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
@@ -844,11 +830,12 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
 }
 
 // --------------------------------------------------------- host launch ----
-int fp_launch_solve(const DevTab* tab, const fp_material* mat, const fp_drive* drv, const fp_tol* tol,
-                    const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
+int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
+                    const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
                     int* d_status, int* d_stats, int grid, cudaStream_t st) {
     KArgs A;
     A.tab = *tab;
+    A.blk = *blk;
     A.mat = *mat;
     A.drv = *drv;
     A.tol = *tol;
@@ -860,15 +847,23 @@ int fp_launch_solve(const DevTab* tab, const fp_material* mat, const fp_drive* d
     A.stats = d_stats;
     A.S_out = drv->output_periods * drv->samples_per_period;
     A.L_launch = L_launch;
-    size_t sm = fp_solver_smem_bytes(L_launch);
-    cudaError_t e = cudaFuncSetAttribute(fp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return FP_ECUDA;
-    fp_solve_kernel<<<grid, NT, sm, st>>>(A);
+    size_t sm = fp_solver_smem_bytes(stages, L_launch);
+    cudaError_t e;
+    if (stages == 5) {
+        e = cudaFuncSetAttribute(fp_solve_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return FP_ECUDA;
+        fp_solve_kernel<5><<<grid, NT, sm, st>>>(A);
+    } else {
+        e = cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return FP_ECUDA;
+        fp_solve_kernel<3><<<grid, NT, sm, st>>>(A);
+    }
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
 }
 
-int fp_upload_constants(const FpRadau* r, const double* glx, const double* glw) {
-    if (cudaMemcpyToSymbol(c_rad, r, sizeof(FpRadau)) != cudaSuccess) return FP_ECUDA;
+int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw) {
+    if (cudaMemcpyToSymbol(c_radau, r3, sizeof(FpRadau), 0) != cudaSuccess) return FP_ECUDA;
+    if (cudaMemcpyToSymbol(c_radau, r5, sizeof(FpRadau), sizeof(FpRadau)) != cudaSuccess) return FP_ECUDA;
     if (cudaMemcpyToSymbol(c_glx, glx, sizeof(double) * FP_NGL) != cudaSuccess) return FP_ECUDA;
     if (cudaMemcpyToSymbol(c_glw, glw, sizeof(double) * FP_NGL) != cudaSuccess) return FP_ECUDA;
     return FP_OK;

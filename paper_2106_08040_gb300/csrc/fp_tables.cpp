@@ -242,104 +242,6 @@ void fp_free_tables(FpTablesHost* t) {
     t->coef = nullptr; t->src = nullptr; t->lam = nullptr; t->wdiag = nullptr; t->tslot = nullptr;
 }
 
-// ---- Radau IIA(5) constants from the collocation definition ----------------
-namespace {
-void inv3(const double A[3][3], double B[3][3]) {
-    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
-               - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
-               + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-    B[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
-    B[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
-    B[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
-    B[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
-    B[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
-    B[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
-    B[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
-    B[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
-    B[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
-}
-}  // namespace
-
-void fp_build_radau(FpRadau* r) {
-    typedef std::complex<double> cd;
-    const double s6 = std::sqrt(6.0);
-    // right Radau points on [0,1] for s = 3: zeros of d^2/dx^2 [x^2 (x-1)^3]
-    //   = 20x^3 - 36x^2 + 18x - 2 = 2 (x - 1)(10x^2 - 8x + 1)
-    r->c[0] = (4.0 - s6) / 10.0;
-    r->c[1] = (4.0 + s6) / 10.0;
-    r->c[2] = 1.0;
-    // a_ij = int_0^{c_i} l_j(x) dx, l_j quadratic Lagrange basis on the nodes
-    for (int j = 0; j < 3; ++j) {
-        int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
-        double den = (r->c[j] - r->c[k1]) * (r->c[j] - r->c[k2]);
-        double q2 = 1.0 / den, q1 = -(r->c[k1] + r->c[k2]) / den, q0 = r->c[k1] * r->c[k2] / den;
-        for (int i = 0; i < 3; ++i) {
-            double x = r->c[i];
-            r->a[i][j] = q2 * x * x * x / 3.0 + q1 * x * x / 2.0 + q0 * x;
-        }
-    }
-    double ai[3][3];
-    inv3(r->a, ai);
-    // eigenvalues of a^{-1}: lambda^3 - t1 lambda^2 + t2 lambda - t3 = 0
-    double t1 = ai[0][0] + ai[1][1] + ai[2][2];
-    double t2 = ai[0][0] * ai[1][1] - ai[0][1] * ai[1][0] + ai[0][0] * ai[2][2] - ai[0][2] * ai[2][0]
-              + ai[1][1] * ai[2][2] - ai[1][2] * ai[2][1];
-    double t3 = ai[0][0] * (ai[1][1] * ai[2][2] - ai[1][2] * ai[2][1])
-              - ai[0][1] * (ai[1][0] * ai[2][2] - ai[1][2] * ai[2][0])
-              + ai[0][2] * (ai[1][0] * ai[2][1] - ai[1][1] * ai[2][0]);
-    double g = t1;                                   // Newton from above on the real root
-    for (int it = 0; it < 200; ++it) {
-        double f = ((g - t1) * g + t2) * g - t3, df = (3.0 * g - 2.0 * t1) * g + t2;
-        double dg = f / df;
-        g -= dg;
-        if (std::fabs(dg) < 1e-16 * std::fabs(g)) break;
-    }
-    // deflate: lambda^2 - (t1 - g) lambda + t3/g = 0
-    double bq = t1 - g, cq = t3 / g;
-    double alp = 0.5 * bq, bet = std::sqrt(cq - alp * alp);
-    r->gam = g; r->alp = alp; r->bet = bet;
-    // eigenvectors: real one and complex one (for alp + i bet) via cross products
-    auto null_real = [&](double lam, double v[3]) {
-        double M[3][3];
-        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) M[i][j] = ai[i][j] - (i == j ? lam : 0.0);
-        v[0] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
-        v[1] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
-        v[2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
-    };
-    double vr[3];
-    null_real(g, vr);
-    cd lam(alp, bet), M[3][3], vc[3];
-    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) M[i][j] = ai[i][j] - (i == j ? lam : cd(0.0));
-    vc[0] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
-    vc[1] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
-    vc[2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
-    for (int i = 0; i < 3; ++i) {
-        r->T[i][0] = vr[i];
-        r->T[i][1] = vc[i].real();
-        r->T[i][2] = vc[i].imag();
-    }
-    inv3(r->T, r->Ti);
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 3; ++k) s += r->Ti[i][k] * ai[k][j];
-            r->K[i][j] = s;
-        }
-    // embedded order-3 formula with an explicit stage at t_n of weight g0 = 1/gam:
-    // sum_{i>=0} bh_i c_i^{q-1} = 1/q (q = 1, 2, 3) with c_0 = 0, bh_0 = g0
-    r->g0 = 1.0 / g;
-    double V[3][3], Vi[3][3], rhs[3] = {1.0 - r->g0, 0.5, 1.0 / 3.0}, bh[3];
-    for (int q = 0; q < 3; ++q) for (int i = 0; i < 3; ++i) V[q][i] = std::pow(r->c[i], q);
-    inv3(V, Vi);
-    for (int i = 0; i < 3; ++i) bh[i] = Vi[i][0] * rhs[0] + Vi[i][1] * rhs[1] + Vi[i][2] * rhs[2];
-    // e = (bh - b)^T a^{-1}, b = last row of a
-    for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
-        for (int i = 0; i < 3; ++i) s += (bh[i] - r->a[2][i]) * ai[i][j];
-        r->e[j] = s;
-    }
-}
-
 // Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n.
 void fp_gauss_legendre(int n, double* x, double* w) {
     const double pi = 3.14159265358979323846;
@@ -360,4 +262,93 @@ void fp_gauss_legendre(int n, double* x, double* w) {
         x[i] = z;
         w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
+}
+
+// ---- block structure for one degree L (rows in block order) ---------------
+namespace {
+inline int slot_group(int k) {     // W, ZR, RZ, RX, RY, GZ, GX, GY
+    return k < 2 ? 0 : k < 4 ? 1 : k < 5 ? 2 : k < 7 ? 3 : k < 9 ? 4 : k < 11 ? 5 : k < 15 ? 6 : 7;
+}
+inline int nblock(int mu, int L) { return mu == 0 ? L + 1 : 2 * (L + 1 - mu); }
+}  // namespace
+
+int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out) {
+    std::memset(out, 0, sizeof(*out));
+    if (L > t->L) return FP_EINVAL;
+    const int N = (L + 1) * (L + 1);
+    out->L = L;
+    out->N = N;
+    out->glob = (int*)std::malloc(sizeof(int) * N);
+    out->sb_k = (unsigned char*)std::malloc((size_t)N * FP_NSB);
+    out->sb_g = (unsigned char*)std::calloc((size_t)N * FP_NSB, 1);
+    out->sb_cf = (float*)std::calloc((size_t)N * FP_NSB, sizeof(float));
+    out->dn_k = (unsigned char*)std::malloc((size_t)N * FP_NLT);
+    out->dn_g = (unsigned char*)std::calloc((size_t)N * FP_NLT, 1);
+    out->dn_cf = (float*)std::calloc((size_t)N * FP_NLT, sizeof(float));
+    out->up_k = (unsigned char*)std::malloc((size_t)N * FP_NLT);
+    out->up_g = (unsigned char*)std::calloc((size_t)N * FP_NLT, 1);
+    out->up_cf = (float*)std::calloc((size_t)N * FP_NLT, sizeof(float));
+    out->dnT = (unsigned char*)std::malloc((size_t)N * FP_NLT);
+    if (!out->glob || !out->sb_k || !out->sb_g || !out->sb_cf || !out->dn_k || !out->dn_g || !out->dn_cf ||
+        !out->up_k || !out->up_g || !out->up_cf || !out->dnT) {
+        fp_free_blocks(out);
+        return FP_ENOMEM;
+    }
+    std::memset(out->sb_k, 255, (size_t)N * FP_NSB);
+    std::memset(out->dn_k, 255, (size_t)N * FP_NLT);
+    std::memset(out->up_k, 255, (size_t)N * FP_NLT);
+    std::memset(out->dnT, 255, (size_t)N * FP_NLT);
+    std::vector<int> boff(L + 2, 0), blk_of(N), loc_of(N), brow(N);
+    for (int mu = 0; mu <= L; ++mu) boff[mu + 1] = boff[mu] + nblock(mu, L);
+    for (int g = 0; g < N; ++g) {
+        int l, m;
+        lm_of(g, l, m);
+        int mu = std::abs(m), k = mu == 0 ? l : 2 * (l - mu) + (m < 0 ? 1 : 0);
+        blk_of[g] = mu;
+        loc_of[g] = k;
+        brow[g] = boff[mu] + k;
+        out->glob[boff[mu] + k] = g;
+    }
+    for (int g = 0; g < N; ++g) {
+        const int b = brow[g], mu = blk_of[g];
+        int nsb = 0, ndn = 0, nup = 0;
+        for (int k = 0; k < FP_NSLOT; ++k) {
+            int j = t->src[g * FP_NSLOT + k];
+            if (j < 0 || j >= N) continue;
+            double cf = t->coef[g * FP_NSLOT + k];
+            if (cf == 0.0) continue;
+            int mj = blk_of[j];
+            unsigned char kj = (unsigned char)loc_of[j], gr = (unsigned char)slot_group(k);
+            if (mj == mu) {
+                out->sb_k[b * FP_NSB + nsb] = kj; out->sb_g[b * FP_NSB + nsb] = gr;
+                out->sb_cf[b * FP_NSB + nsb] = (float)cf; ++nsb;
+            } else if (mj == mu - 1) {
+                out->dn_k[b * FP_NLT + ndn] = kj; out->dn_g[b * FP_NLT + ndn] = gr;
+                out->dn_cf[b * FP_NLT + ndn] = (float)cf; ++ndn;
+            } else if (mj == mu + 1) {
+                out->up_k[b * FP_NLT + nup] = kj; out->up_g[b * FP_NLT + nup] = gr;
+                out->up_cf[b * FP_NLT + nup] = (float)cf; ++nup;
+            }
+            if (nsb > FP_NSB || ndn > FP_NLT || nup > FP_NLT) { fp_free_blocks(out); return FP_EINVAL; }
+        }
+    }
+    // back pointers: for dn partner p of row b, the slot of the partner's up list that points to b
+    for (int b = 0; b < N; ++b) {
+        int g = out->glob[b], mu = blk_of[g];
+        for (int p = 0; p < FP_NLT; ++p) {
+            int kj = out->dn_k[b * FP_NLT + p];
+            if (kj == 255) continue;
+            int bp = boff[mu - 1] + kj;
+            for (int q = 0; q < FP_NLT; ++q)
+                if (out->up_k[bp * FP_NLT + q] == loc_of[g]) { out->dnT[b * FP_NLT + p] = (unsigned char)q; break; }
+        }
+    }
+    return FP_OK;
+}
+
+void fp_free_blocks(FpBlkHost* b) {
+    std::free(b->glob); std::free(b->sb_k); std::free(b->sb_g); std::free(b->sb_cf);
+    std::free(b->dn_k); std::free(b->dn_g); std::free(b->dn_cf);
+    std::free(b->up_k); std::free(b->up_g); std::free(b->up_cf); std::free(b->dnT);
+    std::memset(b, 0, sizeof(*b));
 }

@@ -62,10 +62,18 @@ class Tol:
     newton_max_iter: int = 8
     refactor_every: int = 4
     checkpoint_every: int = 64
+    stages: int = 5
 
     def c(self):
         return fp_tol(self.rtol, self.atol, self.max_steps, self.newton_max_iter,
-                      self.refactor_every, self.checkpoint_every)
+                      self.refactor_every, self.checkpoint_every, self.stages, 0)
+
+
+def fp_peak_fp64():
+    """Measured FP64 FMA throughput of the current device [GFLOP/s]."""
+    v = C.c_double()
+    check(_lib.lib().fp_peak_fp64(C.byref(v)), "fp_peak_fp64")
+    return v.value
 
 
 def fp_max_degree():
