@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-9)
     p.add_argument("--cpu-sample-s", type=float, default=20.0, help="target CPU seconds per oracle process")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--instances", type=int, default=0, help="profiling: first N voxels only (0 = all)")
+    p.add_argument("--warmup-periods", type=int, default=1, help="profiling: warm-up periods per instance")
+    p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
@@ -55,10 +58,16 @@ def dist_env():
     return rank, world, local
 
 
-def workload_for_rank(rank):
+def workload_for_rank(rank, args):
     from paper_2106_08040_gb300 import workloads
     dspec, inst = workloads.system_matrix_workload()
     inst["phi"] = np.deg2rad(15.0 * (rank % 12))
+    if args.instances:
+        inst = inst[:args.instances]
+    if args.warmup_periods != dspec.warmup_periods:
+        d = dict(dspec.__dict__)
+        d["warmup_periods"] = args.warmup_periods
+        dspec = workloads.DriveSpec(**d)
     return dspec, inst
 
 
@@ -179,10 +188,20 @@ def cpu_oracle_sample(dspec, inst, target_s, rtol=1e-10):
     per_sample = max(el / 4, 1e-3)
     ns = int(max(4, min(dspec.samples_per_period, target_s / per_sample)))
     ctx = mp.get_context("spawn")
-    t0 = time.time()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_window, [(dd, inst[k], ns, rtol) for k in picks])
-    wall = time.time() - t0
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"                         # children: single-threaded BLAS, one per core
+    try:
+        t0 = time.time()
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_window, [(dd, inst[k], ns, rtol) for k in picks])
+        wall = time.time() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     ip = sum(r[1] for r in res)
     return {"value": ip / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d voxels of the 32x32 L=16 batch, first %d of 1632 samples of the first period each "
@@ -202,7 +221,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     build.build()
     from paper_2106_08040_gb300 import fp
-    dspec, inst = workload_for_rank(rank)
+    dspec, inst = workload_for_rank(rank, args)
     n = len(inst)
     L = int(inst["L"][0])
     drv = fp.Drive(**dspec.__dict__)
@@ -275,15 +294,17 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.steps):
-        d_inst.copy_(h_inst, non_blocking=True)
-        step()
-        h_ph.copy_(ph, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = float("nan")
+    if not args.no_e2e:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            d_inst.copy_(h_inst, non_blocking=True)
+            step()
+            h_ph.copy_(ph, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         tt = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -294,7 +315,9 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "system_matrix_32x32_L16_lissajous", "instances_per_gpu": n, "L": L,
+            "config": {"workload": "system_matrix_32x32_L16_lissajous" if n == 1024 and periods == 2 else
+                       "system_matrix_L16_lissajous_subset(%d instances, %d periods)" % (n, periods),
+                       "instances_per_gpu": n, "L": L,
                        "periods_per_instance": periods, "samples_per_period": drv.samples_per_period,
                        "radau_stages": args.stages, "rtol": args.rtol, "harmonics": K + 1, "channels": C,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
