@@ -5,7 +5,7 @@ Bar: relative L2 error of the magnetization trace <= 1e-9
 instance).  d<m>/dt = l = 1 rows of A(t) c amplifies the coefficient error by
 ||A|| ~ 1e10 1/s relative to |dm/dt| / |m|, so at the same integrator tolerance
 the derivative, and phi_hat computed from it, carry a larger stated error:
-relative L2 <= 2e-7.  The oracle solves the same Galerkin ODE with an
+relative L2 <= 1e-6.  The oracle solves the same Galerkin ODE with an
 independent integrator (rtol 1e-10..1e-12), the GPU runs at rtol 1e-9.
 """
 import glob
@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD = os.path.join(HERE, "golden")
 TOL = 1e-9          # magnetization trace
-DTOL = 2e-7         # d<m>/dt and phi_hat
+DTOL = 1e-6         # d<m>/dt and phi_hat
 
 
 @pytest.fixture(scope="module")
