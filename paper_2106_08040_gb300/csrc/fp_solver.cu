@@ -129,13 +129,16 @@ template <> __device__ __forceinline__ float czero<float>() { return 0.f; }
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 
 // ------------------------------------------------------------- helpers ----
+// max that keeps NaN visible (fmaxf drops it): a NaN input yields +inf
+__device__ __forceinline__ float nanmax(float a, float b) { return (b != b || a != a) ? __int_as_float(0x7f800000) : fmaxf(a, b); }
+
 __device__ float block_max(float v, float* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULLMASK, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(FULLMASK, v, o));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float r = red[0];
-    for (int i = 1; i < NWARP; ++i) r = fmaxf(r, red[i]);
+    for (int i = 1; i < NWARP; ++i) r = nanmax(r, red[i]);
     return r;
 }
 
@@ -630,10 +633,11 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
         if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, 0.0); jn = 1; }
 
         float ym = 0.f;
-        for (int i = threadIdx.x; i < N; i += NT) ym = fmaxf(ym, fabsf((float)C.y[i]));
+        for (int i = threadIdx.x; i < N; i += NT) ym = nanmax(ym, fabsf((float)C.y[i]));
         double ymax = block_max(ym, s_red);
+        if (!(ymax <= 3.0e38)) status = FP_STATUS_NONFINITE;      // initial state
 
-        while (jn < A.S_out) {
+        while (status == FP_STATUS_OK && jn < A.S_out) {
             if (nsteps + nrej >= A.tol.max_steps) { status = FP_STATUS_MAXSTEPS; break; }
             if (h < 1e-6 * T_s) { status = FP_STATUS_STEP_UNDERFLOW; break; }
             const double tt = sample_time(A.drv, jn);
@@ -745,12 +749,12 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
 #pragma unroll
                         for (int j = 0; j < S; ++j) dz = fmaf((float)RAD<S>().T[k][j], dW[j], dz);
                         C.Z[k * N + i] += (double)dz;
-                        dm = fmaxf(dm, fabsf(dz));
+                        dm = nanmax(dm, fabsf(dz));
                     }
                 }
                 const float dmax = block_max(dm, s_red);
                 ++nit;
-                if (!(dmax < 3.0e38f)) { nonfinite = true; break; }
+                if (!(dmax <= 3.0e38f)) { nonfinite = true; break; }
                 if (it >= 1) {
                     theta = dmax / prev;
                     if (theta >= 0.99f) break;
@@ -782,7 +786,7 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             __syncthreads();
             float em = 0.f;
             const float escale = (float)(RAD<S>().gam * h_f / hs);
-            for (int b = threadIdx.x; b < N; b += NT) em = fmaxf(em, fabsf(escale * C.zr[b]));
+            for (int b = threadIdx.x; b < N; b += NT) em = nanmax(em, fabsf(escale * C.zr[b]));
             const double en = (double)block_max(em, s_red) / sc_err;
             if (!(en < 1e300)) { status = FP_STATUS_NONFINITE; break; }
             const double fac = en > 0.0 ? 0.9 * pow(en, -1.0 / (S + 1)) : 4.0;
@@ -790,9 +794,10 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                 float ymx = 0.f;
                 for (int i = threadIdx.x; i < N; i += NT) {
                     C.y[i] += C.Z[(S - 1) * N + i];
-                    ymx = fmaxf(ymx, fabsf((float)C.y[i]));
+                    ymx = nanmax(ymx, fabsf((float)C.y[i]));
                 }
                 ymax = block_max(ymx, s_red);
+                if (!(ymax <= 3.0e38)) { status = FP_STATUS_NONFINITE; break; }
                 ++nsteps; ++since_fac;
                 t = last ? tt : t + hs;
                 {   // f0 = A(t) y at the accepted point, for the next error estimate
