@@ -55,6 +55,8 @@ struct AScal { double s[8]; };
 
 // ---------------------------------------------------------------- layout ----
 __host__ __device__ inline int nblk(int mu, int L) { return mu == 0 ? L + 1 : 2 * (L + 1 - mu); }
+// column stride of a stored inverse block: odd, so the lanes of a column-split matvec hit distinct banks
+__host__ __device__ inline int ldb(int n) { return n | 1; }
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct Layout {
@@ -71,7 +73,7 @@ __host__ __device__ inline Layout make_layout(int L) {
     ly.N = (L + 1) * (L + 1);
     ly.nmax = (2 * L > L + 1) ? 2 * L : L + 1;
     size_t fsum = 0;
-    for (int mu = 0; mu <= L; ++mu) fsum += (size_t)nblk(mu, L) * nblk(mu, L);
+    for (int mu = 0; mu <= L; ++mu) fsum += (size_t)nblk(mu, L) * ldb(nblk(mu, L));
     ly.fsum = fsum;
     const size_t N = ly.N, nm2 = (size_t)ly.nmax * ly.nmax;
     size_t o = 0;
@@ -79,7 +81,7 @@ __host__ __device__ inline Layout make_layout(int L) {
     ly.Z = o;    o = al16(o + (size_t)S * N * 8);
     ly.F = o;    o = al16(o + (size_t)S * N * 8);
     ly.f0 = o;   o = al16(o + N * 8);
-    ly.yb = o;   o = al16(o + N * 8);
+    ly.yb = o;   o = al16(o + (size_t)S * N * 8);
     ly.diag = o; o = al16(o + N * 8);
     ly.rr = o;   o = al16(o + N * 4);
     ly.zr = o;   o = al16(o + N * 4);
@@ -122,6 +124,12 @@ __device__ __forceinline__ float cshfl(float a, int p) { return __shfl_sync(FULL
 __device__ __forceinline__ float2 cshfl(float2 a, int p) {
     return make_float2(__shfl_sync(FULLMASK, a.x, p), __shfl_sync(FULLMASK, a.y, p));
 }
+__device__ __forceinline__ float cshfl_xor(float a, int o) { return __shfl_xor_sync(FULLMASK, a, o); }
+__device__ __forceinline__ float2 cshfl_xor(float2 a, int o) {
+    return make_float2(__shfl_xor_sync(FULLMASK, a.x, o), __shfl_xor_sync(FULLMASK, a.y, o));
+}
+__device__ __forceinline__ float cadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float cadd_real(float a, float v) { return a + v; }
 __device__ __forceinline__ float2 cadd_real(float2 a, float v) { return make_float2(a.x + v, a.y); }
 template <class T> __device__ __forceinline__ T czero();
@@ -300,7 +308,7 @@ __device__ void group_factor_block(Ctx<S>& C, int mu, T shift, const float* gs, 
             const int j = j0 + jj;
             if (j < n) {
                 const int pj = pp[j];
-                if (pj < n) out[pj * n + myk] = a[jj];       // pj >= n only for a singular block
+                if (pj < n) out[pj * ldb(n) + myk] = a[jj];  // pj >= n only for a singular block
             }
         }
     }
@@ -321,16 +329,22 @@ __device__ __forceinline__ void x_column(Ctx<S>& C, int mu, int c, const T* inv,
         if (k == 255) continue;
         const int q = __ldg(C.dnT + bc * FP_NLT + p);
         const float bv = q == 255 ? 0.f : C.upv[(bo + k) * FP_NLT + q];
-        if (lane < n) acc = cfma(bv, inv[k * n + lane], acc);
+        if (lane < n) acc = cfma(bv, inv[k * ldb(n) + lane], acc);
     }
     if (lane < n) X[lane * n2 + c] = acc;
 }
 
+template <int S> struct Groups {
+    static constexpr int NC = (S - 1) / 2;
+    static constexpr int NSYS = 1 + NC;
+    static constexpr int GW = NWARP / NSYS >= 4 ? 4 : (NWARP / NSYS >= 2 ? 2 : 1);   // warps per system
+};
+
 template <int S>
 __device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2* colbuf) {
-    constexpr int NC = (S - 1) / 2;
-    constexpr int NSYS = 1 + NC;
-    constexpr int GW = NWARP / NSYS >= 4 ? 4 : (NWARP / NSYS >= 2 ? 2 : 1);
+    constexpr int NC = Groups<S>::NC;
+    constexpr int NSYS = Groups<S>::NSYS;
+    constexpr int GW = Groups<S>::GW;
     const int L = C.L, N = C.N;
     float gs[8];
 #pragma unroll
@@ -369,54 +383,62 @@ __device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2*
     }
 }
 
-// ------------------------------------------------------ warp-level solve --
-// Block-Thomas solve of one system with its explicit block inverses: rhs (block
-// order) is overwritten, the solution ends in z.  Called by one full warp.
-template <class T, int S>
-__device__ void warp_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z) {
+// ----------------------------------------------------- warp-group solve --
+// Block-Thomas solve of one system with its explicit block inverses by a group
+// of GW warps: row r of a block is handled by GW lanes (r = gw*RPW + lane%RPW,
+// part = lane/RPW) that split the matvec columns and reduce with shuffles.
+// rhs (block order) is overwritten; the solution ends in z.
+template <class T, int S, int GW>
+__device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, int gw, int barid) {
+    constexpr int RPW = 32 / GW;
     const int lane = threadIdx.x & 31;
+    const int rl = lane % RPW, part = lane / RPW, r = gw * RPW + rl;
     const int L = C.L;
     for (int mu = 0; mu <= L; ++mu) {
-        const int n = nblk(mu, L), bo = C.boff[mu], fo = C.foff[mu];
-        if (lane < n && mu > 0) {
-            const int b = bo + lane, bp = C.boff[mu - 1];
+        const int n = nblk(mu, L), ld = ldb(n), bo = C.boff[mu], fo = C.foff[mu];
+        if (mu > 0 && part == 0 && r < n) {
+            const int b = bo + r, bp = C.boff[mu - 1];
             T v = rhs[b];
 #pragma unroll
             for (int p = 0; p < FP_NLT; ++p) {
-                int k = __ldg(C.dn_k + b * FP_NLT + p);
+                const int k = __ldg(C.dn_k + b * FP_NLT + p);
                 if (k != 255) v = cfma(-C.dnv[b * FP_NLT + p], z[bp + k], v);
             }
             rhs[b] = v;
         }
-        __syncwarp();
-        if (lane < n) {
-            T acc = czero<T>();
-#pragma unroll 8
-            for (int c = 0; c < n; ++c) acc = cfma(inv[fo + c * n + lane], rhs[bo + c], acc);
-            z[bo + lane] = acc;
+        named_bar(barid, 32 * GW);
+        T acc = czero<T>();
+        if (r < n) {
+#pragma unroll 4
+            for (int c = part; c < n; c += GW) acc = cfma(inv[fo + c * ld + r], rhs[bo + c], acc);
         }
-        __syncwarp();
+#pragma unroll
+        for (int o = RPW; o < 32; o <<= 1) acc = cadd(acc, cshfl_xor(acc, o));
+        if (part == 0 && r < n) z[bo + r] = acc;
+        named_bar(barid, 32 * GW);
     }
     for (int mu = L - 1; mu >= 0; --mu) {
-        const int n = nblk(mu, L), bo = C.boff[mu], fo = C.foff[mu], bn = C.boff[mu + 1];
-        if (lane < n) {
-            const int b = bo + lane;
+        const int n = nblk(mu, L), ld = ldb(n), bo = C.boff[mu], fo = C.foff[mu], bn = C.boff[mu + 1];
+        if (part == 0 && r < n) {
+            const int b = bo + r;
             T v = czero<T>();
 #pragma unroll
             for (int p = 0; p < FP_NLT; ++p) {
-                int k = __ldg(C.up_k + b * FP_NLT + p);
+                const int k = __ldg(C.up_k + b * FP_NLT + p);
                 if (k != 255) v = cfma(C.upv[b * FP_NLT + p], z[bn + k], v);
             }
             rhs[b] = v;
         }
-        __syncwarp();
-        if (lane < n) {
-            T acc = czero<T>();
-#pragma unroll 8
-            for (int c = 0; c < n; ++c) acc = cfma(inv[fo + c * n + lane], rhs[bo + c], acc);
-            z[bo + lane] = cfma(-1.f, acc, z[bo + lane]);
+        named_bar(barid, 32 * GW);
+        T acc = czero<T>();
+        if (r < n) {
+#pragma unroll 4
+            for (int c = part; c < n; c += GW) acc = cfma(inv[fo + c * ld + r], rhs[bo + c], acc);
         }
-        __syncwarp();
+#pragma unroll
+        for (int o = RPW; o < 32; o <<= 1) acc = cadd(acc, cshfl_xor(acc, o));
+        if (part == 0 && r < n) z[bo + r] = cfma(-1.f, acc, z[bo + r]);
+        named_bar(barid, 32 * GW);
     }
 }
 
@@ -512,6 +534,8 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
     __shared__ float2 s_colbuf[64 * (1 + NC)];
     __shared__ float s_red[NWARP];
     __shared__ double s_R[9], s_off[3], s_dm[3];
+    __shared__ AScal s_scj[S];          // operator scalars at the stage times
+    __shared__ double s_Pm[S * S];      // predictor matrix
 
     Ctx<S> C;
     C.ly = make_layout<S>(A.L_launch);
@@ -574,7 +598,7 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             int bo = 0, fo = 0;
             for (int mu = 0; mu <= L + 1; ++mu) {
                 s_boff[mu] = bo; s_foff[mu] = fo;
-                if (mu <= L) { int nb = nblk(mu, L); bo += nb; fo += nb * nb; }
+                if (mu <= L) { int nb = nblk(mu, L); bo += nb; fo += nb * ldb(nb); }
             }
             fp_rotation(in.theta, in.phi, s_R);
             for (int k = 0; k < 3; ++k) s_off[k] = in.h_off[k];
@@ -646,31 +670,39 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             if (t + hs >= tt - 1e-12 * T_s) { hs = tt - t; last = true; }
             const double rat = fac_valid ? hs / h_f : 0.0;
             if (!fac_valid || force_refac || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
-                double Bf[3];
-                field_nframe(A, R, off, t + hs, Bf);
-                factorize<S>(C, make_scal(P, Bf), hs, s_pp, s_colbuf);
+                if (threadIdx.x == 0) {
+                    double Bf[3];
+                    field_nframe(A, R, off, t + hs, Bf);
+                    s_scj[0] = make_scal(P, Bf);
+                }
+                __syncthreads();
+                const AScal sf = s_scj[0];
+                __syncthreads();
+                factorize<S>(C, sf, hs, s_pp, s_colbuf);
                 h_f = hs; fac_valid = true; force_refac = false; since_fac = 0; ++nfac;
             }
-            AScal scj[S];
-            for (int j = 0; j < S; ++j) {
-                double Bj[3];
-                field_nframe(A, R, off, t + RAD<S>().c[j] * hs, Bj);
-                scj[j] = make_scal(P, Bj);
+            // per-step scalars, computed once (one lane each) and shared: the operator
+            // scalars at the S stage times and the predictor matrix
+            if (w == 0) {
+                const int lane = threadIdx.x & 31;
+                if (lane < S) {
+                    double Bj[3];
+                    field_nframe(A, R, off, t + RAD<S>().c[lane] * hs, Bj);
+                    s_scj[lane] = make_scal(P, Bj);
+                }
+                if (have_pred && lane < S * S) {
+                    const int i = lane / S, j = lane - i * S;
+                    const double tau_i = 1.0 + RAD<S>().c[i] * (hs / h_old);
+                    const double nj = RAD<S>().c[j];
+                    double lj = tau_i / nj;
+                    for (int k = 0; k < S; ++k)
+                        if (k != j) lj *= (tau_i - RAD<S>().c[k]) / (nj - RAD<S>().c[k]);
+                    s_Pm[lane] = lj - (j == S - 1 ? 1.0 : 0.0);
+                }
             }
+            __syncthreads();
             // predictor from the previous collocation polynomial (nodes 0, c_1..c_S)
             if (have_pred) {
-                const double r = hs / h_old;
-                double Pm[S][S];
-                for (int i = 0; i < S; ++i) {
-                    const double tau_i = 1.0 + RAD<S>().c[i] * r;
-                    for (int j = 0; j < S; ++j) {
-                        const double nj = RAD<S>().c[j];
-                        double lj = tau_i / nj;
-                        for (int k = 0; k < S; ++k)
-                            if (k != j) lj *= (tau_i - RAD<S>().c[k]) / (nj - RAD<S>().c[k]);
-                        Pm[i][j] = lj - (j == S - 1 ? 1.0 : 0.0);
-                    }
-                }
                 for (int i = threadIdx.x; i < N; i += NT) {
                     double zo[S];
 #pragma unroll
@@ -679,7 +711,7 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                     for (int k = 0; k < S; ++k) {
                         double v = 0.0;
 #pragma unroll
-                        for (int j = 0; j < S; ++j) v = fma(Pm[k][j], zo[j], v);
+                        for (int j = 0; j < S; ++j) v = fma(s_Pm[k * S + j], zo[j], v);
                         C.Z[k * N + i] = v;
                     }
                 }
@@ -693,13 +725,14 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             float prev = 3.0e38f, theta = 0.f;
             eta = powf(fmaxf(eta, 1e-7f), 0.8f);
             for (int it = 0; it < A.tol.newton_max_iter; ++it) {
-                // F_j = A(t + c_j h)(y + Z_j), FP64
-                for (int j = 0; j < S; ++j) {
-                    for (int i = threadIdx.x; i < N; i += NT) C.yb[i] = C.y[i] + C.Z[j * N + i];
-                    __syncthreads();
-                    apply_A(C.yb, C.F + j * N, scj[j], C.diag, N, T);
-                    __syncthreads();
+                // F_j = A(t + c_j h)(y + Z_j) for all stages in one pass, FP64
+                for (int e = threadIdx.x; e < S * N; e += NT) C.yb[e] = C.y[e % N] + C.Z[e];
+                __syncthreads();
+                for (int e = threadIdx.x; e < S * N; e += NT) {
+                    const int j = e / N, i = e - j * N;
+                    C.F[e] = apply_row(i, C.yb + j * N, s_scj[j], C.diag, N, T);
                 }
+                __syncthreads();
                 // residual R = -Z + h a F (FP64) -> right-hand sides K R (FP32, block order)
                 for (int b = threadIdx.x; b < N; b += NT) {
                     const int i = __ldg(C.glob + b);
@@ -727,9 +760,14 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                     for (int p = 0; p < NC; ++p) C.rc[p * N + b] = make_float2(q[1 + 2 * p], q[2 + 2 * p]);
                 }
                 __syncthreads();
-                if (w == 0) warp_solve<float, S>(C, C.fr, C.rr, C.zr);
-                else if (w <= NC)
-                    warp_solve<float2, S>(C, C.fc + (size_t)(w - 1) * C.ly.fsum, C.rc + (w - 1) * N, C.zc + (w - 1) * N);
+                {
+                    constexpr int GW = Groups<S>::GW;
+                    const int sys = w / GW, gw = w - sys * GW;
+                    if (sys == 0) group_solve<float, S, GW>(C, C.fr, C.rr, C.zr, gw, 1);
+                    else if (sys <= NC)
+                        group_solve<float2, S, GW>(C, C.fc + (size_t)(sys - 1) * C.ly.fsum, C.rc + (sys - 1) * N,
+                                                   C.zc + (sys - 1) * N, gw, 1 + sys);
+                }
                 __syncthreads();
                 // Z += T dW (h_f / h)
                 float dm = 0.f;
@@ -782,14 +820,14 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                 C.rr[b] = (float)ev;
             }
             __syncthreads();
-            if (w == 0) warp_solve<float, S>(C, C.fr, C.rr, C.zr);
+            if (w < Groups<S>::GW) group_solve<float, S, Groups<S>::GW>(C, C.fr, C.rr, C.zr, w, 1);
             __syncthreads();
             float em = 0.f;
             const float escale = (float)(RAD<S>().gam * h_f / hs);
             for (int b = threadIdx.x; b < N; b += NT) em = nanmax(em, fabsf(escale * C.zr[b]));
             const double en = (double)block_max(em, s_red) / sc_err;
             if (!(en < 1e300)) { status = FP_STATUS_NONFINITE; break; }
-            const double fac = en > 0.0 ? 0.9 * pow(en, -1.0 / (S + 1)) : 4.0;
+            const double fac = en > 0.0 ? 0.9 * (double)powf((float)en, -1.f / (S + 1)) : 4.0;
             if (en <= 1.0) {
                 float ymx = 0.f;
                 for (int i = threadIdx.x; i < N; i += NT) {
@@ -801,9 +839,14 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                 ++nsteps; ++since_fac;
                 t = last ? tt : t + hs;
                 {   // f0 = A(t) y at the accepted point, for the next error estimate
-                    double Bn[3];
-                    field_nframe(A, R, off, t, Bn);
-                    apply_A(C.y, C.f0, make_scal(P, Bn), C.diag, N, T);
+                    if (threadIdx.x == 0) {
+                        double Bn[3];
+                        field_nframe(A, R, off, t, Bn);
+                        s_scj[0] = make_scal(P, Bn);
+                    }
+                    __syncthreads();
+                    const AScal sn = s_scj[0];
+                    apply_A(C.y, C.f0, sn, C.diag, N, T);
                     __syncthreads();
                 }
                 if (last) { write_sample(jn, tt); ++jn; }
