@@ -665,9 +665,12 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             if (nsteps + nrej >= A.tol.max_steps) { status = FP_STATUS_MAXSTEPS; break; }
             if (h < 1e-6 * T_s) { status = FP_STATUS_STEP_UNDERFLOW; break; }
             const double tt = sample_time(A.drv, jn);
-            double hs = fmin(h, T_s);
-            bool last = false;
-            if (t + hs >= tt - 1e-12 * T_s) { hs = tt - t; last = true; }
+            // split the rest of the sample interval into equal steps of at most h, so
+            // the step (and with it the factorisation) changes rarely
+            const double rem = tt - t;
+            const double nrem = ceil(rem / fmin(h, T_s) * (1.0 - 1e-12));
+            const bool last = nrem <= 1.0;
+            const double hs = last ? rem : rem / nrem;
             const double rat = fac_valid ? hs / h_f : 0.0;
             if (!fac_valid || force_refac || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
                 if (threadIdx.x == 0) {
@@ -852,6 +855,8 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
                 if (last) { write_sample(jn, tt); ++jn; }
                 double hn = hs * fmin(4.0, fmax(0.2, fac));
                 if (last && hs < h) hn = fac < 1.0 ? fmin(h, hn) : h;
+                // keep the factorised step when the controller asks for a small change
+                if (fac_valid && hn >= 0.9 * h_f && hn <= 1.2 * h_f) hn = fmax(h_f, hs);
                 h = fmin(hn, T_s);
                 h_old = hs;
                 have_pred = true;

@@ -60,7 +60,7 @@ class Tol:
     atol: float = 1e-15
     max_steps: int = 2_000_000
     newton_max_iter: int = 8
-    refactor_every: int = 4
+    refactor_every: int = 8
     checkpoint_every: int = 64
     stages: int = 5
 
