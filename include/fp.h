@@ -154,6 +154,36 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n,
 int fp_signal(fp_ctx* ctx, const double* d_dmdt, int n, int k_max,
               const double* h_channels, int C, double* d_phihat, void* stream);
 
+/* Device workspace (bytes) that fp_grad needs for n instances: per CTA of the
+ * persistent launch, the recorded step sequence (fp_tol.max_steps steps), one
+ * checkpoint state every 64 steps, one 65-state segment with the stage
+ * increments of its 64 steps, plus the readout cotangents of one period.
+ * Negative FP_E* on error. */
+long long fp_grad_workspace_bytes(const fp_ctx* ctx, int n);
+
+/* Discrete adjoint of the solve + phi_hat map (differentiation of the fixed,
+ * recorded step sequence of the Radau integration; Sec. 2.1 equations as in
+ * fp_solve_batch, readout of Sec. 2.2).  Given the cotangent
+ *   d_dJ_dphihat [n][C][k_max+1][2] = (dJ/dRe phi_hat, dJ/dIm phi_hat)
+ * of a real scalar J, writes
+ *   d_grad [n][4] = (dJ/dK, dJ/dd, dJ/dtheta, dJ/dphi)
+ * per instance (K in J/m^3, d in m, angles in rad).  The forward pass is
+ * re-run inside with checkpoints every 64 steps; each 64-step segment is
+ * replayed, and every step's transposed collocation system is solved with FP64
+ * residuals.  The initial-state term uses central differences of the Boltzmann
+ * projection.  h_channels, C, k_max as in fp_signal.  d_status as in
+ * fp_solve_batch; d_stats [n][4] or NULL: forward accepted steps, forward
+ * rejected steps, the phase that failed (0 none, 1 forward pass, 2 segment
+ * replay, 3 transposed stage solve) and the step index where it failed (-1 if
+ * none).  Gradients of instances whose status is not FP_STATUS_OK are 0.
+ * d_work: device workspace of
+ * work_bytes >= fp_grad_workspace_bytes(ctx, n), owned by the caller, contents
+ * undefined on return.  Asynchronous on `stream`. */
+int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
+            const double* h_channels, int C, const double* d_dJ_dphihat,
+            double* d_grad, int* d_status, int* d_stats, void* d_work,
+            unsigned long long work_bytes, void* stream);
+
 /* Diagnostic (host only, no GPU needed): dense Galerkin matrix A of
  * dc/dt = A c (Eq. FP-general tested against the real SH basis) for one
  * instance in the EASY-AXIS frame (n = z), with the field B_nframe [T] already

@@ -15,6 +15,12 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
                     int* d_status, int* d_stats, int grid, cudaStream_t st);
 int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw);
+size_t fp_adjoint_smem_bytes(int stages, int L);
+size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec);
+int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
+                      const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, int k_max,
+                      const double* channels, int C, const double* d_dJ, const double* d_tw, double* d_grad,
+                      int* d_status, int* d_stats, double* d_work, int max_rec, int grid, cudaStream_t st);
 
 struct fp_ctx {
     fp_material mat;
@@ -28,6 +34,7 @@ struct fp_ctx {
     int* d_src;
     double* d_lam;
     double* d_wdiag;
+    FpPair* d_colT;           // column view of the tables (adjoint)
     DevBlk blk;               // device block structure, all degrees 2..L_max
     void* d_blk_mem;          // one allocation backing blk
     double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
@@ -78,6 +85,7 @@ int fp_destroy(fp_ctx* ctx) {
     cudaFree(ctx->d_src);
     cudaFree(ctx->d_blk_mem);
     cudaFree(ctx->d_lam);
+    cudaFree(ctx->d_colT);
     cudaFree(ctx->d_wdiag);
     cudaFree(ctx->d_tw);
     fp_free_tables(&ctx->host);
@@ -121,6 +129,11 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
     up((void**)&c->d_src, c->host.src, N * FP_NSLOT * sizeof(int));
     up((void**)&c->d_lam, c->host.lam, N * sizeof(double));
     up((void**)&c->d_wdiag, c->host.wdiag, N * sizeof(double));
+    {
+        std::vector<FpPair> colT(N * FP_NCT);
+        if (fp_build_columns(&c->host, colT.data()) != FP_OK) { fp_destroy(c); return fail(FP_EINVAL, "fp_setup: columns"); }
+        up((void**)&c->d_colT, colT.data(), colT.size() * sizeof(FpPair));
+    }
     std::vector<double> tw(2 * (size_t)drive->samples_per_period);
     const double twopi = 6.283185307179586476925286766559;
     for (int q = 0; q < drive->samples_per_period; ++q) {
@@ -146,9 +159,9 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
         }
         const size_t b_glob = rows * 4, b_u8 = rows * FP_NSB, b_f8 = rows * FP_NSB * 4, b_u6 = rows * FP_NLT,
                      b_f6 = rows * FP_NLT * 4;
-        size_t offs[11], o = 0;
-        const size_t sizes[11] = {b_glob, b_u8, b_u8, b_f8, b_u6, b_u6, b_f6, b_u6, b_u6, b_f6, b_u6};
-        for (int q = 0; q < 11; ++q) { offs[q] = o; o += (sizes[q] + 255) & ~(size_t)255; }
+        size_t offs[12], o = 0;
+        const size_t sizes[12] = {b_glob, b_u8, b_u8, b_f8, b_u6, b_u6, b_f6, b_u6, b_u6, b_f6, b_u6, b_u6};
+        for (int q = 0; q < 12; ++q) { offs[q] = o; o += (sizes[q] + 255) & ~(size_t)255; }
         std::vector<unsigned char> hb(o, 0);
         for (int L = 2; L <= L_max; ++L) {
             const FpBlkHost& b = bl[L];
@@ -164,6 +177,7 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
             std::memcpy(&hb[offs[8] + r0 * FP_NLT], b.up_g, b.N * FP_NLT);
             std::memcpy(&hb[offs[9] + r0 * FP_NLT * 4], b.up_cf, b.N * FP_NLT * 4);
             std::memcpy(&hb[offs[10] + r0 * FP_NLT], b.dnT, b.N * FP_NLT);
+            std::memcpy(&hb[offs[11] + r0 * FP_NLT], b.upT, b.N * FP_NLT);
             fp_free_blocks(&bl[L]);
         }
         up(&c->d_blk_mem, hb.data(), o);
@@ -180,6 +194,7 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
         c->blk.up_g = base + offs[8];
         c->blk.up_cf = (const float*)(base + offs[9]);
         c->blk.dnT = base + offs[10];
+        c->blk.upT = base + offs[11];
     }
     FpRadau r3, r5;
     if (fp_build_radau(3, &r3) != FP_OK || fp_build_radau(5, &r5) != FP_OK) {
@@ -204,7 +219,7 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     if (n < 0) return fail(FP_EINVAL, "fp_solve_batch: n < 0");
     if (n == 0) return FP_OK;
     if (!d_inst || !d_status) return fail(FP_EINVAL, "fp_solve_batch: NULL instance or status buffer");
-    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag};
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT};
     size_t sm = fp_solver_smem_bytes(ctx->tol.stages, ctx->L_max);
     int max_sm = 0;
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -214,6 +229,40 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     int rc = fp_launch_solve(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
                              d_m, d_dmdt, d_status, d_stats, grid, (cudaStream_t)stream);
     if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return FP_OK;
+}
+
+long long fp_grad_workspace_bytes(const fp_ctx* ctx, int n) {
+    if (!ctx || n < 0) return fail(FP_EINVAL, "fp_grad_workspace_bytes: bad argument");
+    const int grid = n < ctx->num_sms ? n : ctx->num_sms;
+    return (long long)grid * 8LL *
+           (long long)fp_adjoint_work_doubles_per_cta(ctx->tol.stages, ctx->L_max, ctx->drv.samples_per_period, ctx->tol.max_steps);
+}
+
+int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max, const double* h_channels, int C,
+            const double* d_dJ_dphihat, double* d_grad, int* d_status, int* d_stats, void* d_work,
+            unsigned long long work_bytes, void* stream) {
+    if (!ctx) return fail(FP_EINVAL, "fp_grad: NULL ctx");
+    if (n < 0) return fail(FP_EINVAL, "fp_grad: n < 0");
+    if (n == 0) return FP_OK;
+    if (!d_inst || !d_dJ_dphihat || !d_grad || !d_status || !h_channels || !d_work)
+        return fail(FP_EINVAL, "fp_grad: NULL buffer");
+    if (k_max < 0 || k_max >= ctx->drv.samples_per_period) return fail(FP_EINVAL, "fp_grad: k_max=%d", k_max);
+    if (C < 1 || C > 4) return fail(FP_EINVAL, "fp_grad: C=%d outside [1, 4]", C);
+    const long long need = fp_grad_workspace_bytes(ctx, n);
+    if ((long long)work_bytes < need)
+        return fail(FP_EINVAL, "fp_grad: workspace %llu bytes < %lld needed", work_bytes, need);
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT};
+    size_t sm = fp_adjoint_smem_bytes(ctx->tol.stages, ctx->L_max);
+    int max_sm = 0;
+    cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if ((int)sm > max_sm)
+        return fail(FP_EUNSUPPORTED, "fp_grad: %zu bytes of shared memory needed, %d available", sm, max_sm);
+    const int grid = n < ctx->num_sms ? n : ctx->num_sms;
+    int rc = fp_launch_adjoint(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n,
+                               ctx->L_max, k_max, h_channels, C, d_dJ_dphihat, ctx->d_tw, d_grad, d_status, d_stats,
+                               (double*)d_work, ctx->tol.max_steps, grid, (cudaStream_t)stream);
+    if (rc != FP_OK) return fail(rc, "fp_grad: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }
 

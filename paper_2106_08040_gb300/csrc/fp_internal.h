@@ -113,8 +113,11 @@ struct FpBlkHost {
     unsigned char* up_g;
     float* up_cf;
     unsigned char* dnT;        // [N][FP_NLT]
+    unsigned char* upT;        // [N][FP_NLT] for each up partner: position in its dn list of the coupling back
 };
 int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out);
+
+struct FpPair { int row, slot; };
 
 // Device views of the tables (pointers into context-owned device memory).
 #include <stdint.h>
@@ -123,6 +126,7 @@ struct DevTab {
     const int* src;
     const double* lam;
     const double* wdiag;
+    const FpPair* colT;              // [N][FP_NCT] column view (row, slot)
 };
 struct DevBlk {                      // block structure of every degree, packed
     const int* glob;
@@ -136,7 +140,13 @@ struct DevBlk {                      // block structure of every degree, packed
     const uint8_t* up_g;
     const float* up_cf;
     const uint8_t* dnT;
+    const uint8_t* upT;
     int off[FP_L_MAX + 2];           // first packed row of degree L
 };
+
+// Column view of the coupling tables (for A^T x): for column i, up to FP_NCT
+// (row, slot) pairs with table[row][slot] having source i; row = -1 pads.
+#define FP_NCT 24
+int fp_build_columns(const FpTablesHost* t, FpPair* out);   // out: [N][FP_NCT]
 void fp_free_blocks(FpBlkHost* b);
 void fp_gauss_legendre(int n, double* x, double* w);

@@ -61,11 +61,12 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15
 
 struct Layout {
     int N, L, nmax;
-    size_t y, Z, F, f0, yb, diag, rr, zr, rc, zc, dnv, upv, fr, fc, Xr, Xc, ic, total;
+    size_t y, Z, F, f0, yb, diag, rr, zr, rc, zc, dnv, upv, fr, fc, Xr, Xc, lam, aw, ic, total;
     size_t fsum;
 };
 
-template <int S>
+// ADJ adds the adjoint state lambda (N) and one more stage-sized buffer (S N).
+template <int S, bool ADJ = false>
 __host__ __device__ inline Layout make_layout(int L) {
     constexpr int NC = (S - 1) / 2;
     Layout ly;
@@ -93,6 +94,8 @@ __host__ __device__ inline Layout make_layout(int L) {
     ly.fc = o;   o = al16(o + (size_t)NC * fsum * 8);
     ly.Xr = o;   o = al16(o + nm2 * 4);
     ly.Xc = o;   o = al16(o + (size_t)NC * nm2 * 8);
+    ly.lam = o;  if (ADJ) o = al16(o + N * 8);
+    ly.aw = o;   if (ADJ) o = al16(o + (size_t)S * N * 8);
     ly.ic = ly.fr;                                     // initial-state scratch aliases the factors
     size_t ic_end = ly.ic + (size_t)FP_NGL * (L + 1) * 8;
     ly.total = o > ic_end ? o : al16(ic_end);
@@ -101,6 +104,9 @@ __host__ __device__ inline Layout make_layout(int L) {
 
 size_t fp_solver_smem_bytes(int stages, int L) {
     return stages == 5 ? make_layout<5>(L).total : make_layout<3>(L).total;
+}
+size_t fp_adjoint_smem_bytes(int stages, int L) {
+    return stages == 5 ? make_layout<5, true>(L).total : make_layout<3, true>(L).total;
 }
 
 // --------------------------------------------------- scalar/complex ops ----
@@ -201,7 +207,7 @@ template <int S>
 struct Ctx {
     Layout ly;
     int L, N;
-    double *y, *Z, *F, *f0, *yb, *diag;
+    double *y, *Z, *F, *f0, *yb, *diag, *lam, *aw;
     float *rr, *zr;
     float2 *rc, *zc;
     float *dnv, *upv;
@@ -213,7 +219,7 @@ struct Ctx {
     int* foff;
     // block structure of degree L
     const int* glob;
-    const uint8_t *sb_k, *sb_g, *dn_k, *dn_g, *up_k, *up_g, *dnT;
+    const uint8_t *sb_k, *sb_g, *dn_k, *dn_g, *up_k, *up_g, *dnT, *upT;
     const float *sb_cf, *dn_cf, *up_cf;
 };
 
@@ -388,8 +394,11 @@ __device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2*
 // of GW warps: row r of a block is handled by GW lanes (r = gw*RPW + lane%RPW,
 // part = lane/RPW) that split the matvec columns and reduce with shuffles.
 // rhs (block order) is overwritten; the solution ends in z.
-template <class T, int S, int GW>
+template <class T, int S, int GW, bool TRANS>
 __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, int gw, int barid) {
+    // TRANS solves M^T x = b with the same factors: the forward sweep uses
+    // B^T (values reached through dnT), the backward sweep C^T (through upT) and
+    // the block inverses transposed.
     constexpr int RPW = 32 / GW;
     const int lane = threadIdx.x & 31;
     const int rl = lane % RPW, part = lane / RPW, r = gw * RPW + rl;
@@ -402,7 +411,15 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
 #pragma unroll
             for (int p = 0; p < FP_NLT; ++p) {
                 const int k = __ldg(C.dn_k + b * FP_NLT + p);
-                if (k != 255) v = cfma(-C.dnv[b * FP_NLT + p], z[bp + k], v);
+                if (k == 255) continue;
+                float cv;
+                if (TRANS) {
+                    const int q = __ldg(C.dnT + b * FP_NLT + p);
+                    cv = q == 255 ? 0.f : C.upv[(bp + k) * FP_NLT + q];
+                } else {
+                    cv = C.dnv[b * FP_NLT + p];
+                }
+                v = cfma(-cv, z[bp + k], v);
             }
             rhs[b] = v;
         }
@@ -410,7 +427,8 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
         T acc = czero<T>();
         if (r < n) {
 #pragma unroll 4
-            for (int c = part; c < n; c += GW) acc = cfma(inv[fo + c * ld + r], rhs[bo + c], acc);
+            for (int c = part; c < n; c += GW)
+                acc = cfma(inv[fo + (TRANS ? r * ld + c : c * ld + r)], rhs[bo + c], acc);
         }
 #pragma unroll
         for (int o = RPW; o < 32; o <<= 1) acc = cadd(acc, cshfl_xor(acc, o));
@@ -425,7 +443,15 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
 #pragma unroll
             for (int p = 0; p < FP_NLT; ++p) {
                 const int k = __ldg(C.up_k + b * FP_NLT + p);
-                if (k != 255) v = cfma(C.upv[b * FP_NLT + p], z[bn + k], v);
+                if (k == 255) continue;
+                float cv;
+                if (TRANS) {
+                    const int q = __ldg(C.upT + b * FP_NLT + p);
+                    cv = q == 255 ? 0.f : C.dnv[(bn + k) * FP_NLT + q];
+                } else {
+                    cv = C.upv[b * FP_NLT + p];
+                }
+                v = cfma(cv, z[bn + k], v);
             }
             rhs[b] = v;
         }
@@ -433,7 +459,8 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
         T acc = czero<T>();
         if (r < n) {
 #pragma unroll 4
-            for (int c = part; c < n; c += GW) acc = cfma(inv[fo + c * ld + r], rhs[bo + c], acc);
+            for (int c = part; c < n; c += GW)
+                acc = cfma(inv[fo + (TRANS ? r * ld + c : c * ld + r)], rhs[bo + c], acc);
         }
 #pragma unroll
         for (int o = RPW; o < 32; o <<= 1) acc = cadd(acc, cshfl_xor(acc, o));
@@ -450,9 +477,9 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
 // backward ratio recurrence r_mu = k / (2 mu + k r_{mu+1}) normalised with
 // e^k = I_0 + 2 sum_mu I_mu.
 template <int S>
-__device__ void initial_state(Ctx<S>& C, const FpParams& P, const double* B, unsigned char* smem) {
+__device__ void initial_state(Ctx<S>& C, const FpParams& P, const double* B, unsigned char* smem, double* out) {
     const int L = C.L;
-    double* E = (double*)(smem + C.ly.ic);   // [FP_NGL][L+1]
+    double* E = (double*)(smem + C.ly.ic);   // [FP_NGL][L+1]; aliases the factor storage
     const double pi = 3.14159265358979323846;
     double Bp = sqrt(B[0] * B[0] + B[1] * B[1]);
     double Babs = sqrt(Bp * Bp + B[2] * B[2]);
@@ -508,15 +535,15 @@ __device__ void initial_state(Ctx<S>& C, const FpParams& P, const double* B, uns
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULLMASK, part, o);
             if (lane == 0) {
                 int g0 = l * l + l;
-                if (mu == 0) C.y[g0] = part;
-                else { C.y[g0 + mu] = sq2 * part * cphi; C.y[g0 - mu] = sq2 * part * sphi; }
+                if (mu == 0) out[g0] = part;
+                else { out[g0 + mu] = sq2 * part * cphi; out[g0 - mu] = sq2 * part * sphi; }
             }
         }
     }
     __syncthreads();
-    double norm = 1.0 / (C.y[0] * sqrt(4.0 * pi));
+    double norm = 1.0 / (out[0] * sqrt(4.0 * pi));
     __syncthreads();
-    for (int i = threadIdx.x; i < C.N; i += NT) C.y[i] *= norm;
+    for (int i = threadIdx.x; i < C.N; i += NT) out[i] *= norm;
     __syncthreads();
 }
 
@@ -525,20 +552,22 @@ __device__ __forceinline__ double sample_time(const fp_drive& d, int j) {
     return ((double)d.warmup_periods + (double)j / (double)d.samples_per_period) * d.period;
 }
 
+// Shared (per-CTA) scalars of the instance being integrated.
 template <int S>
-__global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
-    constexpr int NC = (S - 1) / 2;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_boff[FP_L_MAX + 2], s_foff[FP_L_MAX + 2];
-    __shared__ int s_pp[32 * (1 + NC)];
-    __shared__ float2 s_colbuf[64 * (1 + NC)];
-    __shared__ float s_red[NWARP];
-    __shared__ double s_R[9], s_off[3], s_dm[3];
-    __shared__ AScal s_scj[S];          // operator scalars at the stage times
-    __shared__ double s_Pm[S * S];      // predictor matrix
+struct Shared {
+    int boff[FP_L_MAX + 2], foff[FP_L_MAX + 2];
+    int pp[32 * (1 + (S - 1) / 2)];
+    float2 colbuf[64 * (1 + (S - 1) / 2)];
+    float red[NWARP];
+    double dred[NWARP * 12];
+    double R[9], off[3], dm[3];
+    AScal scj[S];          // operator scalars at the stage times
+    double Pm[S * S];      // predictor matrix
+};
 
-    Ctx<S> C;
-    C.ly = make_layout<S>(A.L_launch);
+template <int S, bool ADJ>
+__device__ void bind_smem(Ctx<S>& C, unsigned char* smem, int L_launch, Shared<S>& sh) {
+    C.ly = make_layout<S, ADJ>(L_launch);
     C.y = (double*)(smem + C.ly.y);
     C.Z = (double*)(smem + C.ly.Z);
     C.F = (double*)(smem + C.ly.F);
@@ -555,17 +584,392 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
     C.fc = (float2*)(smem + C.ly.fc);
     C.Xr = (float*)(smem + C.ly.Xr);
     C.Xc = (float2*)(smem + C.ly.Xc);
-    C.boff = s_boff;
-    C.foff = s_foff;
-    const DevTab& T = A.tab;
-    const double sq43 = sqrt(4.0 * 3.14159265358979323846 / 3.0);
-    const int w = threadIdx.x >> 5;
+    C.lam = (double*)(smem + C.ly.lam);
+    C.aw = (double*)(smem + C.ly.aw);
+    C.boff = sh.boff;
+    C.foff = sh.foff;
+}
 
+__device__ __forceinline__ bool instance_ok(const fp_instance& in, int L_launch) {
+    return in.L >= 2 && in.L <= L_launch && in.d > 0.0 && in.K >= 0.0 && in.flags == 0;
+}
+
+// Per-instance setup: block structure pointers and offsets, rotation, offset
+// field, FP64 diagonal of A.  Returns the Neel constants.
+template <int S>
+__device__ FpParams setup_instance(Ctx<S>& C, const KArgs& A, const fp_instance& in, Shared<S>& sh) {
+    const int L = in.L;
+    C.L = L;
+    C.N = (L + 1) * (L + 1);
+    const int o = A.blk.off[L];
+    C.glob = A.blk.glob + o;
+    C.sb_k = A.blk.sb_k + (size_t)o * FP_NSB;
+    C.sb_g = A.blk.sb_g + (size_t)o * FP_NSB;
+    C.sb_cf = A.blk.sb_cf + (size_t)o * FP_NSB;
+    C.dn_k = A.blk.dn_k + (size_t)o * FP_NLT;
+    C.dn_g = A.blk.dn_g + (size_t)o * FP_NLT;
+    C.dn_cf = A.blk.dn_cf + (size_t)o * FP_NLT;
+    C.up_k = A.blk.up_k + (size_t)o * FP_NLT;
+    C.up_g = A.blk.up_g + (size_t)o * FP_NLT;
+    C.up_cf = A.blk.up_cf + (size_t)o * FP_NLT;
+    C.dnT = A.blk.dnT + (size_t)o * FP_NLT;
+    C.upT = A.blk.upT + (size_t)o * FP_NLT;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int bo = 0, fo = 0;
+        for (int mu = 0; mu <= L + 1; ++mu) {
+            sh.boff[mu] = bo; sh.foff[mu] = fo;
+            if (mu <= L) { int nb = nblk(mu, L); bo += nb; fo += nb * ldb(nb); }
+        }
+        fp_rotation(in.theta, in.phi, sh.R);
+        for (int k = 0; k < 3; ++k) sh.off[k] = in.h_off[k];
+    }
+    __syncthreads();
+    const FpParams P = fp_derive(A.mat, in.K, in.d);
+    for (int i = threadIdx.x; i < C.N; i += NT)
+        C.diag[i] = -P.D * __ldg(A.tab.lam + i) - 0.5 * P.p4 * __ldg(A.tab.wdiag + i);
+    __syncthreads();
+    return P;
+}
+
+// Simplified Newton iteration for the collocation stages Z (in C.Z, initial
+// guess already set) of the step (t, hs) from C.y; stage scalars in sh.scj.
+struct NewtonResult { bool conv, nonfinite; float theta, dmax; int iters; };
+
+template <int S>
+__device__ NewtonResult newton_stages(Ctx<S>& C, const DevTab& T, double hs, double h_f, double sc_err, float& eta,
+                                      float kappa, int maxit, Shared<S>& sh) {
+    constexpr int NC = (S - 1) / 2;
+    const int N = C.N, w = threadIdx.x >> 5;
+    const float fscale = (float)(h_f / hs);
+    NewtonResult res{false, false, 0.f, 0.f, 0};
+    float prev = 3.0e38f;
+    eta = powf(fmaxf(eta, 1e-7f), 0.8f);
+    for (int it = 0; it < maxit; ++it) {
+        // F_j = A(t + c_j h)(y + Z_j) for all stages in one pass, FP64
+        for (int e = threadIdx.x; e < S * N; e += NT) C.yb[e] = C.y[e % N] + C.Z[e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < S * N; e += NT) {
+            const int j = e / N, i = e - j * N;
+            C.F[e] = apply_row(i, C.yb + j * N, sh.scj[j], C.diag, N, T);
+        }
+        __syncthreads();
+        // residual R = -Z + h a F (FP64) -> right-hand sides K R (FP32, block order)
+        for (int b = threadIdx.x; b < N; b += NT) {
+            const int i = __ldg(C.glob + b);
+            double fv[S];
+            float Rk[S];
+#pragma unroll
+            for (int j = 0; j < S; ++j) fv[j] = C.F[j * N + i];
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < S; ++j) acc = fma(RAD<S>().a[k][j], fv[j], acc);
+                Rk[k] = (float)fma(hs, acc, -C.Z[k * N + i]);
+            }
+            float q[S];
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < S; ++j) acc = fmaf((float)RAD<S>().K[k][j], Rk[j], acc);
+                q[k] = acc;
+            }
+            C.rr[b] = q[0];
+#pragma unroll
+            for (int p = 0; p < NC; ++p) C.rc[p * N + b] = make_float2(q[1 + 2 * p], q[2 + 2 * p]);
+        }
+        __syncthreads();
+        {
+            constexpr int GW = Groups<S>::GW;
+            const int sys = w / GW, gw = w - sys * GW;
+            if (sys == 0) group_solve<float, S, GW, false>(C, C.fr, C.rr, C.zr, gw, 1);
+            else if (sys <= NC)
+                group_solve<float2, S, GW, false>(C, C.fc + (size_t)(sys - 1) * C.ly.fsum, C.rc + (sys - 1) * N,
+                                                  C.zc + (sys - 1) * N, gw, 1 + sys);
+        }
+        __syncthreads();
+        // Z += T dW (h_f / h)
+        float dm = 0.f;
+        for (int b = threadIdx.x; b < N; b += NT) {
+            const int i = __ldg(C.glob + b);
+            float dW[S];
+            dW[0] = fscale * C.zr[b];
+#pragma unroll
+            for (int p = 0; p < NC; ++p) {
+                float2 v = C.zc[p * N + b];
+                dW[1 + 2 * p] = fscale * v.x;
+                dW[2 + 2 * p] = fscale * v.y;
+            }
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                float dz = 0.f;
+#pragma unroll
+                for (int j = 0; j < S; ++j) dz = fmaf((float)RAD<S>().T[k][j], dW[j], dz);
+                C.Z[k * N + i] += (double)dz;
+                dm = nanmax(dm, fabsf(dz));
+            }
+        }
+        const float dmax = block_max(dm, sh.red);
+        ++res.iters;
+        res.dmax = dmax;
+        if (!(dmax <= 3.0e38f)) { res.nonfinite = true; break; }
+        if (it >= 1) {
+            res.theta = dmax / prev;
+            if (res.theta >= 0.99f) break;
+            eta = res.theta / (1.f - res.theta);
+        }
+        if (eta * dmax <= kappa * (float)sc_err || dmax <= 1e-3f * kappa * (float)sc_err) { res.conv = true; break; }
+        prev = dmax;
+    }
+    return res;
+}
+
+// operator scalars at the S stage times of (t, hs) and, if pred, the
+// predictor matrix; one lane each, shared through sh
+template <int S>
+__device__ void stage_scalars(const KArgs& A, const FpParams& P, const double* R, const double* off, double t,
+                              double hs, bool pred, double h_old, Shared<S>& sh) {
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        if (lane < S) {
+            double Bj[3];
+            field_nframe(A, R, off, t + RAD<S>().c[lane] * hs, Bj);
+            sh.scj[lane] = make_scal(P, Bj);
+        }
+        if (pred && lane < S * S) {
+            const int i = lane / S, j = lane - i * S;
+            const double tau_i = 1.0 + RAD<S>().c[i] * (hs / h_old);
+            const double nj = RAD<S>().c[j];
+            double lj = tau_i / nj;
+            for (int k = 0; k < S; ++k)
+                if (k != j) lj *= (tau_i - RAD<S>().c[k]) / (nj - RAD<S>().c[k]);
+            sh.Pm[lane] = lj - (j == S - 1 ? 1.0 : 0.0);
+        }
+    }
+    __syncthreads();
+}
+
+template <int S>
+__device__ void predict_stages(Ctx<S>& C, bool pred, Shared<S>& sh) {
+    const int N = C.N;
+    if (pred) {
+        for (int i = threadIdx.x; i < N; i += NT) {
+            double zo[S];
+#pragma unroll
+            for (int j = 0; j < S; ++j) zo[j] = C.Z[j * N + i];
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                double v = 0.0;
+#pragma unroll
+                for (int j = 0; j < S; ++j) v = fma(sh.Pm[k * S + j], zo[j], v);
+                C.Z[k * N + i] = v;
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < S * N; i += NT) C.Z[i] = 0.0;
+    }
+    __syncthreads();
+}
+
+// factorise the iteration matrices for step hs ending at t + hs
+template <int S>
+__device__ void refactor(Ctx<S>& C, const KArgs& A, const FpParams& P, const double* R, const double* off, double t,
+                         double hs, Shared<S>& sh) {
+    if (threadIdx.x == 0) {
+        double Bf[3];
+        field_nframe(A, R, off, t + hs, Bf);
+        sh.scj[0] = make_scal(P, Bf);
+    }
+    __syncthreads();
+    const AScal sf = sh.scj[0];
+    __syncthreads();
+    factorize<S>(C, sf, hs, sh.pp, sh.colbuf);
+}
+
+// Adaptive integration of one instance over the whole schedule.  SOLVE mode
+// writes <m>, d<m>/dt at every sample; REC mode instead records every accepted
+// step (t, h, sample index or -1) in rec_steps and the state before every
+// CKPT-th step in rec_ckpt.
+#define FP_CKPT 64
+struct FwdOut { int status, nsteps, nrej, nit, nfac; };
+
+template <int S, bool REC>
+__device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const FpParams& P, Shared<S>& sh,
+                                   double* rec_steps, double* rec_ckpt, int max_rec) {
+    const DevTab& T = A.tab;
+    const int N = C.N;
+    const double sq43 = sqrt(4.0 * 3.14159265358979323846 / 3.0);
+    double R[9], off[3];
+    for (int k = 0; k < 9; ++k) R[k] = sh.R[k];
+    for (int k = 0; k < 3; ++k) off[k] = sh.off[k];
+    double B[3];
+    field_nframe(A, R, off, 0.0, B);
+    initial_state<S>(C, P, B, (unsigned char*)C.y - C.ly.y, C.y);
+
+    const double T_s = A.drv.period / A.drv.samples_per_period;     // sample spacing = h_max
+    const double rtol = A.tol.rtol, atol = A.tol.atol;
+    double t = 0.0;
+    double h = fmin(T_s, 0.01 * (0.5 / P.D));
+    FwdOut out{FP_STATUS_OK, 0, 0, 0, 0};
+    int jn = 0;
+    bool have_pred = false, fac_valid = false, force_refac = false;
+    int since_fac = 0;
+    double h_f = 0.0, h_old = 0.0;
+    float eta = 1.0f;
+
+    {
+        const AScal sc0 = make_scal(P, B);
+        apply_A(C.y, C.f0, sc0, C.diag, N, T);                 // f0 = A(t) y
+        __syncthreads();
+    }
+    auto write_sample = [&](int j, double tj) {
+        if (REC) return;
+        // <m> and d<m>/dt at t_j (l = 1 rows of A(t_j) y), rotated back to the lab frame
+        if (threadIdx.x < 3) {
+            double Bs[3];
+            field_nframe(A, R, off, tj, Bs);
+            AScal ss = make_scal(P, Bs);
+            int row = threadIdx.x == 0 ? 3 : threadIdx.x;   // x' <- (1,1), y' <- (1,-1), z' <- (1,0)
+            sh.dm[threadIdx.x] = sq43 * apply_row(row, C.y, ss, C.diag, N, T);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double mp[3] = {sq43 * C.y[3], sq43 * C.y[1], sq43 * C.y[2]};
+            double dp[3] = {sh.dm[0], sh.dm[1], sh.dm[2]};
+            size_t o = ((size_t)inst * A.S_out + j) * 3;
+            for (int k = 0; k < 3; ++k) {
+                double mk = R[k] * mp[0] + R[3 + k] * mp[1] + R[6 + k] * mp[2];
+                double dk = R[k] * dp[0] + R[3 + k] * dp[1] + R[6 + k] * dp[2];
+                if (A.m_out) A.m_out[o + k] = mk;
+                if (A.dmdt_out) A.dmdt_out[o + k] = dk;
+            }
+        }
+        __syncthreads();
+    };
+
+    if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, 0.0); jn = 1; }
+
+    float ym = 0.f;
+    for (int i = threadIdx.x; i < N; i += NT) ym = nanmax(ym, fabsf((float)C.y[i]));
+    double ymax = block_max(ym, sh.red);
+    if (!(ymax <= 3.0e38)) out.status = FP_STATUS_NONFINITE;      // initial state
+
+    while (out.status == FP_STATUS_OK && jn < A.S_out) {
+        if (out.nsteps + out.nrej >= A.tol.max_steps || (REC && out.nsteps >= max_rec)) {
+            out.status = FP_STATUS_MAXSTEPS;
+            break;
+        }
+        if (h < 1e-6 * T_s) { out.status = FP_STATUS_STEP_UNDERFLOW; break; }
+        const double tt = sample_time(A.drv, jn);
+        // split the rest of the sample interval into equal steps of at most h, so
+        // the step (and with it the factorisation) changes rarely
+        const double rem = tt - t;
+        const double nrem = ceil(rem / fmin(h, T_s) * (1.0 - 1e-12));
+        const bool last = nrem <= 1.0;
+        const double hs = last ? rem : rem / nrem;
+        const double rat = fac_valid ? hs / h_f : 0.0;
+        if (!fac_valid || force_refac || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
+            refactor<S>(C, A, P, R, off, t, hs, sh);
+            h_f = hs; fac_valid = true; force_refac = false; since_fac = 0; ++out.nfac;
+        }
+        if (REC && out.nsteps % FP_CKPT == 0) {       // checkpoint the state before this step
+            double* ck = rec_ckpt + (size_t)(out.nsteps / FP_CKPT) * N;
+            for (int i = threadIdx.x; i < N; i += NT) ck[i] = C.y[i];
+        }
+        stage_scalars<S>(A, P, R, off, t, hs, have_pred, h_old, sh);
+        predict_stages<S>(C, have_pred, sh);
+        const double sc_err = atol + rtol * ymax;
+        const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_err, eta, 0.02f, A.tol.newton_max_iter, sh);
+        out.nit += nr.iters;
+        if (nr.nonfinite) { out.status = FP_STATUS_NONFINITE; break; }
+        if (!nr.conv) {
+            ++out.nrej;
+            if (since_fac == 0 && hs <= 1e-6 * T_s) { out.status = FP_STATUS_NEWTON_FAIL; break; }
+            if (since_fac == 0) h = hs * 0.5;      // fresh factors did not converge: shrink the step
+            have_pred = false; force_refac = true; eta = 1.0f;
+            __syncthreads();
+            continue;
+        }
+        if (nr.theta > 0.1f) force_refac = true;   // slow contraction: refresh the factors next step
+        // embedded error estimate, filtered through the real factor
+        for (int b = threadIdx.x; b < N; b += NT) {
+            const int i = __ldg(C.glob + b);
+            double ev = hs * RAD<S>().g0 * C.f0[i];
+#pragma unroll
+            for (int j = 0; j < S; ++j) ev = fma(RAD<S>().e[j], C.Z[j * N + i], ev);
+            C.rr[b] = (float)ev;
+        }
+        __syncthreads();
+        if ((threadIdx.x >> 5) < Groups<S>::GW)
+            group_solve<float, S, Groups<S>::GW, false>(C, C.fr, C.rr, C.zr, threadIdx.x >> 5, 1);
+        __syncthreads();
+        float em = 0.f;
+        const float escale = (float)(RAD<S>().gam * h_f / hs);
+        for (int b = threadIdx.x; b < N; b += NT) em = nanmax(em, fabsf(escale * C.zr[b]));
+        const double en = (double)block_max(em, sh.red) / sc_err;
+        if (!(en < 1e300)) { out.status = FP_STATUS_NONFINITE; break; }
+        const double fac = en > 0.0 ? 0.9 * (double)powf((float)en, -1.f / (S + 1)) : 4.0;
+        if (en <= 1.0) {
+            if (REC && threadIdx.x == 0) {
+                double* r = rec_steps + (size_t)out.nsteps * 3;
+                r[0] = t; r[1] = hs; r[2] = last ? (double)jn : -1.0;
+            }
+            float ymx = 0.f;
+            for (int i = threadIdx.x; i < N; i += NT) {
+                C.y[i] += C.Z[(S - 1) * N + i];
+                ymx = nanmax(ymx, fabsf((float)C.y[i]));
+            }
+            ymax = block_max(ymx, sh.red);
+            if (!(ymax <= 3.0e38)) { out.status = FP_STATUS_NONFINITE; break; }
+            ++out.nsteps; ++since_fac;
+            t = last ? tt : t + hs;
+            {   // f0 = A(t) y at the accepted point, for the next error estimate
+                if (threadIdx.x == 0) {
+                    double Bn[3];
+                    field_nframe(A, R, off, t, Bn);
+                    sh.scj[0] = make_scal(P, Bn);
+                }
+                __syncthreads();
+                const AScal sn = sh.scj[0];
+                apply_A(C.y, C.f0, sn, C.diag, N, T);
+                __syncthreads();
+            }
+            if (last) { write_sample(jn, tt); ++jn; }
+            double hn = hs * fmin(4.0, fmax(0.2, fac));
+            if (last && hs < h) hn = fac < 1.0 ? fmin(h, hn) : h;
+            // keep the factorised step when the controller asks for a small change
+            if (fac_valid && hn >= 0.9 * h_f && hn <= 1.2 * h_f) hn = fmax(h_f, hs);
+            h = fmin(hn, T_s);
+            h_old = hs;
+            have_pred = true;
+        } else {
+            ++out.nrej;
+            h = hs * fmax(0.1, fac);
+            have_pred = false;
+        }
+        __syncthreads();
+    }
+    if (!REC) {
+        for (int e = jn * 3 + threadIdx.x; e < A.S_out * 3; e += NT) {
+            if (A.m_out) A.m_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
+            if (A.dmdt_out) A.dmdt_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
+        }
+    }
+    __syncthreads();
+    return out;
+}
+
+template <int S>
+__global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared<S> sh;
+    Ctx<S> C;
+    bind_smem<S, false>(C, smem, A.L_launch, sh);
     for (int inst = blockIdx.x; inst < A.n; inst += gridDim.x) {
         const fp_instance in = A.inst[inst];
-        const int L = in.L;
-        const bool bad = !(L >= 2 && L <= A.L_launch && in.d > 0.0 && in.K >= 0.0 && in.flags == 0);
-        if (bad) {
+        if (!instance_ok(in, A.L_launch)) {
             for (int e = threadIdx.x; e < A.S_out * 3; e += NT) {
                 if (A.m_out) A.m_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
                 if (A.dmdt_out) A.dmdt_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
@@ -576,307 +980,502 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             }
             continue;
         }
-        C.L = L;
-        C.N = (L + 1) * (L + 1);
-        const int N = C.N;
-        {
-            const int o = A.blk.off[L];
-            C.glob = A.blk.glob + o;
-            C.sb_k = A.blk.sb_k + (size_t)o * FP_NSB;
-            C.sb_g = A.blk.sb_g + (size_t)o * FP_NSB;
-            C.sb_cf = A.blk.sb_cf + (size_t)o * FP_NSB;
-            C.dn_k = A.blk.dn_k + (size_t)o * FP_NLT;
-            C.dn_g = A.blk.dn_g + (size_t)o * FP_NLT;
-            C.dn_cf = A.blk.dn_cf + (size_t)o * FP_NLT;
-            C.up_k = A.blk.up_k + (size_t)o * FP_NLT;
-            C.up_g = A.blk.up_g + (size_t)o * FP_NLT;
-            C.up_cf = A.blk.up_cf + (size_t)o * FP_NLT;
-            C.dnT = A.blk.dnT + (size_t)o * FP_NLT;
-        }
-        __syncthreads();
+        const FpParams P = setup_instance<S>(C, A, in, sh);
+        const FwdOut o = forward_instance<S, false>(C, A, inst, P, sh, nullptr, nullptr, 0);
         if (threadIdx.x == 0) {
-            int bo = 0, fo = 0;
-            for (int mu = 0; mu <= L + 1; ++mu) {
-                s_boff[mu] = bo; s_foff[mu] = fo;
-                if (mu <= L) { int nb = nblk(mu, L); bo += nb; fo += nb * ldb(nb); }
+            A.status[inst] = o.status;
+            if (A.stats) {
+                A.stats[inst * 4 + 0] = o.nsteps; A.stats[inst * 4 + 1] = o.nrej;
+                A.stats[inst * 4 + 2] = o.nit;    A.stats[inst * 4 + 3] = o.nfac;
             }
-            fp_rotation(in.theta, in.phi, s_R);
-            for (int k = 0; k < 3; ++k) s_off[k] = in.h_off[k];
         }
         __syncthreads();
-        const FpParams P = fp_derive(A.mat, in.K, in.d);
-        double R[9], off[3];
-        for (int k = 0; k < 9; ++k) R[k] = s_R[k];
-        for (int k = 0; k < 3; ++k) off[k] = s_off[k];
-        for (int i = threadIdx.x; i < N; i += NT)
-            C.diag[i] = -P.D * __ldg(T.lam + i) - 0.5 * P.p4 * __ldg(T.wdiag + i);
+    }
+}
 
-        double B[3];
-        field_nframe(A, R, off, 0.0, B);
-        initial_state<S>(C, P, B, smem);
+// ============================================================ adjoint =======
+// Discrete adjoint of the Radau integration (frozen step sequence).  With
+// G = I - h (a x I) blkdiag(A_j) the step is c_{n+1} = e_S^T G^{-1} (1 x c_n), so
+//   G^T zeta = e_S x lambda_{n+1},  lambda_n = sum_i zeta_i,
+//   dJ/dp += h sum_j xi_j^T (dA_j/dp) Y_j,  xi_j = sum_i a_ij zeta_i,
+// plus the readout terms at the sample times and the initial-state term.
 
-        const double T_s = A.drv.period / A.drv.samples_per_period;     // sample spacing = h_max
-        const double rtol = A.tol.rtol, atol = A.tol.atol;
-        const float kappa = 0.02f;
-        double t = 0.0;
-        double h = fmin(T_s, 0.01 * (0.5 / P.D));
-        int jn = 0, nsteps = 0, nrej = 0, nit = 0, nfac = 0, status = FP_STATUS_OK;
-        bool have_pred = false, fac_valid = false, force_refac = false;
-        int since_fac = 0;
-        double h_f = 0.0, h_old = 0.0;
-        float eta = 1.0f;
+// row i of A^T x (FP64) from the column view of the tables
+__device__ __forceinline__ double apply_row_T(int i, const double* __restrict__ x, const AScal& sc,
+                                              const double* __restrict__ diag, int N, const DevTab& T) {
+    double acc = diag[i] * x[i];
+#pragma unroll 4
+    for (int q = 0; q < FP_NCT; ++q) {
+        const FpPair pr = T.colT[(size_t)i * FP_NCT + q];
+        if ((unsigned)pr.row >= (unsigned)N) continue;
+        acc = fma(sc.s[grp_of(pr.slot)] * __ldg(T.coef + (size_t)pr.row * FP_NSLOT + pr.slot), x[pr.row], acc);
+    }
+    return acc;
+}
 
-        AScal sc0 = make_scal(P, B);
-        apply_A(C.y, C.f0, sc0, C.diag, N, T);            // f0 = A(t) y
-        __syncthreads();
+// derivative scalars of A w.r.t. (K, d, theta, phi) at lab field Blab:
+// A = dl*Lap + dw*Wdiag + sum_g s_g T_g with dl = -D, dw = -p4/2
+struct DScal { double s[8]; double dl, dw; };
 
-        auto write_sample = [&](int j, double tj) {
-            // <m> and d<m>/dt at t_j (l = 1 rows of A(t_j) y), rotated back to the lab frame
-            if (threadIdx.x < 3) {
-                double Bs[3];
-                field_nframe(A, R, off, tj, Bs);
-                AScal ss = make_scal(P, Bs);
-                int row = threadIdx.x == 0 ? 3 : threadIdx.x;   // x' <- (1,1), y' <- (1,-1), z' <- (1,0)
-                s_dm[threadIdx.x] = sq43 * apply_row(row, C.y, ss, C.diag, N, T);
+__device__ void dscal_all(const fp_material& mt, const FpParams& P, double d, double th, double ph, const double* Blab,
+                          DScal* out) {
+    const double gt = mt.gamma / (1.0 + mt.alpha * mt.alpha);
+    for (int q = 0; q < 4; ++q) {
+        for (int g = 0; g < 8; ++g) out[q].s[g] = 0.0;
+        out[q].dl = 0.0;
+        out[q].dw = 0.0;
+    }
+    // K: p3 = 2 gt K / Ms, p4 = alpha p3
+    out[0].s[0] = -mt.alpha * gt / mt.Ms;
+    out[0].s[1] = -2.0 * gt / mt.Ms;
+    out[0].dw = -mt.alpha * gt / mt.Ms;
+    // d: D ~ d^-3
+    out[1].dl = 3.0 * P.D / d;
+    // angles: B' = R(theta, phi) Blab
+    const double ct = cos(th), st = sin(th), cp = cos(ph), sp = sin(ph);
+    const double dRt[9] = {-st * cp, -st * sp, -ct, 0.0, 0.0, 0.0, ct * cp, ct * sp, -st};
+    const double dRp[9] = {-ct * sp, ct * cp, 0.0, -cp, -sp, 0.0, -st * sp, st * cp, 0.0};
+    for (int q = 0; q < 2; ++q) {
+        const double* dR = q == 0 ? dRt : dRp;
+        double Bp[3];
+        for (int r = 0; r < 3; ++r) Bp[r] = dR[3 * r] * Blab[0] + dR[3 * r + 1] * Blab[1] + dR[3 * r + 2] * Blab[2];
+        DScal& o = out[2 + q];
+        o.s[2] = -P.p1 * Bp[2]; o.s[3] = -P.p1 * Bp[0]; o.s[4] = -P.p1 * Bp[1];
+        o.s[5] = -P.p2 * Bp[2]; o.s[6] = -P.p2 * Bp[0]; o.s[7] = -P.p2 * Bp[1];
+    }
+}
+
+__device__ void lab_field(const KArgs& A, const double* off, double t, double* Bl) {
+    const double twopi = 6.283185307179586476925286766559;
+    for (int k = 0; k < 3; ++k) Bl[k] = off[k] + A.drv.amp[k] * sin(twopi * A.drv.freq[k] * t + A.drv.phase[k]);
+}
+
+// block reduction of 10 doubles per thread; every thread gets the sums
+__device__ void block_sum10(double* v, double* red) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(FULLMASK, v[q], o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 10; ++q) red[(threadIdx.x >> 5) * 12 + q] = v[q];
+    __syncthreads();
+    for (int q = 0; q < 10; ++q) {
+        double s = 0.0;
+        for (int w = 0; w < NWARP; ++w) s += red[w * 12 + q];
+        v[q] = s;
+    }
+    __syncthreads();
+}
+
+// bilinear forms xi^T T_g y per scalar group g (8), xi^T Lap y, xi^T Wdiag y
+__device__ void bilinear(const double* xi, const double* yv, int N, const DevTab& T, double* beta) {
+    for (int q = 0; q < 10; ++q) beta[q] = 0.0;
+    for (int i = threadIdx.x; i < N; i += NT) {
+        const double xv = xi[i];
+        const double* cf = T.coef + (size_t)i * FP_NSLOT;
+        const int* sr = T.src + (size_t)i * FP_NSLOT;
+#pragma unroll
+        for (int k = 0; k < FP_NSLOT; ++k) {
+            int j = __ldg(sr + k);
+            double v = ((unsigned)j < (unsigned)N) ? yv[j] : 0.0;
+            beta[grp_of(k)] = fma(xv * __ldg(cf + k), v, beta[grp_of(k)]);
+        }
+        beta[8] = fma(xv * __ldg(T.lam + i), yv[i], beta[8]);
+        beta[9] = fma(xv * __ldg(T.wdiag + i), yv[i], beta[9]);
+    }
+}
+
+__device__ __forceinline__ double dot_dscal(const DScal& d, const double* beta) {
+    double s = d.dl * beta[8] + d.dw * beta[9];
+    for (int g = 0; g < 8; ++g) s = fma(d.s[g], beta[g], s);
+    return s;
+}
+
+// Readout at a sample time: u_c = p_c . R^T sqrt(4pi/3) (A(t) c)_{l=1} with the lab
+// cotangent g = sum_c (dJ/du_c) p_c.  Adds A^T-term to lambda, direct terms to grad.
+template <int S>
+__device__ void readout_adjoint(Ctx<S>& C, const KArgs& A, const FpParams& P, const fp_instance& in, const double* R,
+                                const double* off, double t, const double* g, const double* cst, double* grad,
+                                Shared<S>& sh) {
+    const DevTab& T = A.tab;
+    const int N = C.N;
+    const double sq43 = sqrt(4.0 * 3.14159265358979323846 / 3.0);
+    if (threadIdx.x == 0) {
+        double Bl[3], Bp[3];
+        lab_field(A, off, t, Bl);
+        for (int r = 0; r < 3; ++r) Bp[r] = R[3 * r] * Bl[0] + R[3 * r + 1] * Bl[1] + R[3 * r + 2] * Bl[2];
+        const AScal sc = make_scal(P, Bp);
+        // v' = R g in the easy-axis frame, rows (1,1), (1,-1), (1,0) = x', y', z'
+        double vp[3];
+        for (int r = 0; r < 3; ++r) vp[r] = R[3 * r] * g[0] + R[3 * r + 1] * g[1] + R[3 * r + 2] * g[2];
+        const int rows[3] = {3, 1, 2};
+        // lambda += sqrt(4pi/3) A^T e with e_rows = vp  (scatter over the three rows' couplings)
+        for (int q = 0; q < 3; ++q) {
+            const int r = rows[q];
+            const double e = sq43 * vp[q];
+            C.lam[r] = fma(C.diag[r], e, C.lam[r]);
+            for (int k = 0; k < FP_NSLOT; ++k) {
+                int j = __ldg(T.src + (size_t)r * FP_NSLOT + k);
+                if ((unsigned)j >= (unsigned)N) continue;
+                C.lam[j] = fma(sc.s[grp_of(k)] * __ldg(T.coef + (size_t)r * FP_NSLOT + k), e, C.lam[j]);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double mp[3] = {sq43 * C.y[3], sq43 * C.y[1], sq43 * C.y[2]};
-                double dp[3] = {s_dm[0], s_dm[1], s_dm[2]};
-                size_t o = ((size_t)inst * A.S_out + j) * 3;
+        }
+        // direct parameter terms: g . dR^T/dp m'dot + sqrt(4pi/3) vp . ((dA/dp) c)_rows
+        double mdot[3];
+        for (int q = 0; q < 3; ++q) mdot[q] = sq43 * apply_row(rows[q], cst, sc, C.diag, N, T);
+        DScal ds[4];
+        dscal_all(A.mat, P, in.d, in.theta, in.phi, Bl, ds);
+        const double ct = cos(in.theta), stt = sin(in.theta), cp = cos(in.phi), sp = sin(in.phi);
+        const double dRt[9] = {-stt * cp, -stt * sp, -ct, 0.0, 0.0, 0.0, ct * cp, ct * sp, -stt};
+        const double dRp[9] = {-ct * sp, ct * cp, 0.0, -cp, -sp, 0.0, -stt * sp, stt * cp, 0.0};
+        for (int p = 0; p < 4; ++p) {
+            double acc = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const int r = rows[q];
+                double dr = ds[p].dl * __ldg(T.lam + r) * cst[r] + ds[p].dw * __ldg(T.wdiag + r) * cst[r];
+                for (int k = 0; k < FP_NSLOT; ++k) {
+                    int j = __ldg(T.src + (size_t)r * FP_NSLOT + k);
+                    if ((unsigned)j >= (unsigned)N) continue;
+                    dr = fma(ds[p].s[grp_of(k)] * __ldg(T.coef + (size_t)r * FP_NSLOT + k), cst[j], dr);
+                }
+                acc = fma(sq43 * vp[q], dr, acc);
+            }
+            if (p >= 2) {   // rotation of the output back to the lab frame: m = R^T m'
+                const double* dR = p == 2 ? dRt : dRp;
                 for (int k = 0; k < 3; ++k) {
-                    double mk = R[k] * mp[0] + R[3 + k] * mp[1] + R[6 + k] * mp[2];
-                    double dk = R[k] * dp[0] + R[3 + k] * dp[1] + R[6 + k] * dp[2];
-                    if (A.m_out) A.m_out[o + k] = mk;
-                    if (A.dmdt_out) A.dmdt_out[o + k] = dk;
+                    double dm = dR[k] * mdot[0] + dR[3 + k] * mdot[1] + dR[6 + k] * mdot[2];
+                    acc = fma(g[k], dm, acc);
                 }
             }
-            __syncthreads();
-        };
+            grad[p] += acc;
+        }
+    }
+    __syncthreads();
+}
 
-        if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, 0.0); jn = 1; }
+// transposed stage solve: G^T zeta = e_S x lambda, zeta in C.F; stages Z (for the
+// stage times) unchanged; factors current.  Returns the iteration count, -1 on a
+// non-finite value, -2 when the iteration stalls or does not converge.
+template <int S>
+__device__ int adjoint_stages(Ctx<S>& C, const DevTab& T, double hs, double h_f, int maxit, Shared<S>& sh) {
+    constexpr int NC = (S - 1) / 2;
+    const int N = C.N, w = threadIdx.x >> 5;
+    const float fscale = (float)(h_f / hs);
+    for (int i = threadIdx.x; i < S * N; i += NT) C.F[i] = 0.0;
+    float lm = 0.f;
+    for (int i = threadIdx.x; i < N; i += NT) lm = nanmax(lm, fabsf((float)C.lam[i]));
+    const float lmax = block_max(lm, sh.red);
+    if (lmax == 0.f) return 0;
+    if (!(lmax <= 3.0e38f)) return -1;
+    float prev = 3.0e38f;
+    for (int it = 0; it < maxit; ++it) {
+        // v_i = sum_j a_ji zeta_j ; w_i = A_i^T v_i
+        for (int e = threadIdx.x; e < S * N; e += NT) {
+            const int i = e / N, r = e - i * N;
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < S; ++j) acc = fma(RAD<S>().a[j][i], C.F[j * N + r], acc);
+            C.yb[e] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < S * N; e += NT) {
+            const int i = e / N, r = e - i * N;
+            C.aw[e] = apply_row_T(r, C.yb + i * N, sh.scj[i], C.diag, N, T);
+        }
+        __syncthreads();
+        // rho_i = delta_iS lambda - zeta_i + h w_i  -> q = Lam^T T^T rho (FP32)
+        for (int b = threadIdx.x; b < N; b += NT) {
+            const int r = __ldg(C.glob + b);
+            float rho[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                double v = fma(hs, C.aw[i * N + r], -C.F[i * N + r]);
+                if (i == S - 1) v += C.lam[r];
+                rho[i] = (float)v;
+            }
+            float tr[S];           // T^T rho
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < S; ++i) acc = fmaf((float)RAD<S>().T[i][k], rho[i], acc);
+                tr[k] = acc;
+            }
+            // Lam^T: real gam; pairs [[alp, -bet], [bet, alp]]
+            C.rr[b] = (float)RAD<S>().gam * tr[0];
+#pragma unroll
+            for (int p = 0; p < NC; ++p) {
+                const float al = (float)RAD<S>().alp[p], be = (float)RAD<S>().bet[p];
+                const float q1 = al * tr[1 + 2 * p] - be * tr[2 + 2 * p];
+                const float q2 = be * tr[1 + 2 * p] + al * tr[2 + 2 * p];
+                C.rc[p * N + b] = make_float2(q1, -q2);        // conjugated for the transposed complex solve
+            }
+        }
+        __syncthreads();
+        {
+            constexpr int GW = Groups<S>::GW;
+            const int sys = w / GW, gw = w - sys * GW;
+            if (sys == 0) group_solve<float, S, GW, true>(C, C.fr, C.rr, C.zr, gw, 1);
+            else if (sys <= NC)
+                group_solve<float2, S, GW, true>(C, C.fc + (size_t)(sys - 1) * C.ly.fsum, C.rc + (sys - 1) * N,
+                                                 C.zc + (sys - 1) * N, gw, 1 + sys);
+        }
+        __syncthreads();
+        // zeta += T^{-T} omega (h_f / h)
+        float dm = 0.f;
+        for (int b = threadIdx.x; b < N; b += NT) {
+            const int r = __ldg(C.glob + b);
+            float om[S];
+            om[0] = fscale * C.zr[b];
+#pragma unroll
+            for (int p = 0; p < NC; ++p) {
+                float2 v = C.zc[p * N + b];
+                om[1 + 2 * p] = fscale * v.x;
+                om[2 + 2 * p] = -fscale * v.y;                  // conjugate back
+            }
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                float dz = 0.f;
+#pragma unroll
+                for (int j = 0; j < S; ++j) dz = fmaf((float)RAD<S>().Ti[j][k], om[j], dz);
+                C.F[k * N + r] += (double)dz;
+                dm = nanmax(dm, fabsf(dz));
+            }
+        }
+        const float dmax = block_max(dm, sh.red);
+        if (!(dmax <= 3.0e38f)) return -1;
+        if (dmax <= 1e-11f * lmax) return it + 1;
+        if (it >= 2 && dmax > 0.99f * prev) return dmax <= 1e-8f * lmax ? it + 1 : -2;   // stagnated
+        prev = dmax;
+    }
+    return -2;
+}
 
-        float ym = 0.f;
-        for (int i = threadIdx.x; i < N; i += NT) ym = nanmax(ym, fabsf((float)C.y[i]));
-        double ymax = block_max(ym, s_red);
-        if (!(ymax <= 3.0e38)) status = FP_STATUS_NONFINITE;      // initial state
+struct GArgs {
+    KArgs A;
+    const double* dJ;       // [n][C][K+1][2]
+    double* grad;           // [n][4]
+    const double* tw;       // twiddles [S_p][2]
+    double ch[4][3];
+    int C, K;
+    double* work;           // per CTA: work_per_cta doubles
+    size_t work_per_cta;
+    int max_rec;
+};
 
-        while (status == FP_STATUS_OK && jn < A.S_out) {
-            if (nsteps + nrej >= A.tol.max_steps) { status = FP_STATUS_MAXSTEPS; break; }
-            if (h < 1e-6 * T_s) { status = FP_STATUS_STEP_UNDERFLOW; break; }
-            const double tt = sample_time(A.drv, jn);
-            // split the rest of the sample interval into equal steps of at most h, so
-            // the step (and with it the factorisation) changes rarely
-            const double rem = tt - t;
-            const double nrem = ceil(rem / fmin(h, T_s) * (1.0 - 1e-12));
-            const bool last = nrem <= 1.0;
-            const double hs = last ? rem : rem / nrem;
-            const double rat = fac_valid ? hs / h_f : 0.0;
-            if (!fac_valid || force_refac || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
-                if (threadIdx.x == 0) {
-                    double Bf[3];
-                    field_nframe(A, R, off, t + hs, Bf);
-                    s_scj[0] = make_scal(P, Bf);
+template <int S>
+__global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared<S> sh;
+    __shared__ double s_g[3], s_grad[4];
+    const KArgs& A = G.A;
+    const DevTab& T = A.tab;
+    Ctx<S> C;
+    bind_smem<S, true>(C, smem, A.L_launch, sh);
+    const int Sp = A.drv.samples_per_period, j0 = A.S_out - Sp;
+    const int Nmax = (A.L_launch + 1) * (A.L_launch + 1);
+    double* ws = G.work + (size_t)blockIdx.x * G.work_per_cta;
+    double* ws_steps = ws;                                              // [max_rec][3]
+    double* ws_ckpt = ws_steps + (size_t)G.max_rec * 3;                 // [max_rec/CKPT + 1][Nmax]
+    double* ws_seg = ws_ckpt + (size_t)(G.max_rec / FP_CKPT + 1) * Nmax; // [CKPT + 1][Nmax]
+    double* ws_g = ws_seg + (size_t)(FP_CKPT + 1) * Nmax;                // [Sp][3]
+    double* ws_Z = ws_g + (size_t)Sp * 3;                                // [CKPT][S][Nmax] stage increments
+
+    for (int inst = blockIdx.x; inst < A.n; inst += gridDim.x) {
+        const fp_instance in = A.inst[inst];
+        if (!instance_ok(in, A.L_launch)) {
+            if (threadIdx.x < 4) G.grad[inst * 4 + threadIdx.x] = 0.0;
+            if (threadIdx.x == 0) A.status[inst] = FP_STATUS_BAD_INPUT;
+            continue;
+        }
+        const FpParams P = setup_instance<S>(C, A, in, sh);
+        const int N = C.N;
+        double R[9], off[3];
+        for (int k = 0; k < 9; ++k) R[k] = sh.R[k];
+        for (int k = 0; k < 3; ++k) off[k] = sh.off[k];
+        // (1) dJ/du_c(t_j) over the last period, as lab vectors g_j = sum_c (dJ/du_c) p_c
+        for (int j = threadIdx.x; j < Sp; j += NT) {
+            double gv[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c < G.C; ++c) {
+                const double* dj = G.dJ + (((size_t)inst * G.C + c) * (G.K + 1)) * 2;
+                double acc = 0.0;
+                int q = 0;
+                for (int k = 0; k <= G.K; ++k) {
+                    acc = fma(dj[2 * k], G.tw[2 * q], acc);
+                    acc = fma(-dj[2 * k + 1], G.tw[2 * q + 1], acc);
+                    q += j;
+                    if (q >= Sp) q -= Sp;
                 }
-                __syncthreads();
-                const AScal sf = s_scj[0];
-                __syncthreads();
-                factorize<S>(C, sf, hs, s_pp, s_colbuf);
-                h_f = hs; fac_valid = true; force_refac = false; since_fac = 0; ++nfac;
+                acc /= (double)Sp;
+                for (int k = 0; k < 3; ++k) gv[k] = fma(acc, G.ch[c][k], gv[k]);
             }
-            // per-step scalars, computed once (one lane each) and shared: the operator
-            // scalars at the S stage times and the predictor matrix
-            if (w == 0) {
-                const int lane = threadIdx.x & 31;
-                if (lane < S) {
-                    double Bj[3];
-                    field_nframe(A, R, off, t + RAD<S>().c[lane] * hs, Bj);
-                    s_scj[lane] = make_scal(P, Bj);
-                }
-                if (have_pred && lane < S * S) {
-                    const int i = lane / S, j = lane - i * S;
-                    const double tau_i = 1.0 + RAD<S>().c[i] * (hs / h_old);
-                    const double nj = RAD<S>().c[j];
-                    double lj = tau_i / nj;
-                    for (int k = 0; k < S; ++k)
-                        if (k != j) lj *= (tau_i - RAD<S>().c[k]) / (nj - RAD<S>().c[k]);
-                    s_Pm[lane] = lj - (j == S - 1 ? 1.0 : 0.0);
-                }
+            for (int k = 0; k < 3; ++k) ws_g[j * 3 + k] = gv[k];
+        }
+        __syncthreads();
+        // (2) forward pass recording steps and checkpoints
+        const FwdOut fo = forward_instance<S, true>(C, A, inst, P, sh, ws_steps, ws_ckpt, G.max_rec);
+        int status = fo.status;
+        const int nacc = fo.nsteps;
+        if (threadIdx.x < 4) s_grad[threadIdx.x] = 0.0;
+        for (int i = threadIdx.x; i < N; i += NT) C.lam[i] = 0.0;
+        __syncthreads();
+        // (3) backward sweep, segment by segment
+        double sc_rep = A.tol.atol;                // replay Newton tolerance, set per segment
+        bool fac_valid = false;
+        double h_f = 0.0;
+        int since_fac = 0, fail_phase = 0, fail_step = -1;
+        const int nseg = (nacc + FP_CKPT - 1) / FP_CKPT;
+        for (int sg = nseg - 1; sg >= 0 && status == FP_STATUS_OK; --sg) {
+            const int n0 = sg * FP_CKPT, n1 = min(nacc, n0 + FP_CKPT);
+            // replay the segment from its checkpoint, keeping every state and
+            // every step's stage increments
+            float ym = 0.f;
+            for (int i = threadIdx.x; i < N; i += NT) {
+                C.y[i] = ws_ckpt[(size_t)sg * N + i]; ws_seg[i] = C.y[i];
+                ym = nanmax(ym, fabsf((float)C.y[i]));
             }
-            __syncthreads();
-            // predictor from the previous collocation polynomial (nodes 0, c_1..c_S)
-            if (have_pred) {
-                for (int i = threadIdx.x; i < N; i += NT) {
-                    double zo[S];
-#pragma unroll
-                    for (int j = 0; j < S; ++j) zo[j] = C.Z[j * N + i];
-#pragma unroll
-                    for (int k = 0; k < S; ++k) {
-                        double v = 0.0;
-#pragma unroll
-                        for (int j = 0; j < S; ++j) v = fma(s_Pm[k * S + j], zo[j], v);
-                        C.Z[k * N + i] = v;
-                    }
+            // the forward's Newton tolerance: replayed states stay within the
+            // forward's own iteration error of the recorded path
+            sc_rep = A.tol.atol + A.tol.rtol * (double)block_max(ym, sh.red);
+            fac_valid = false;                     // the last factors belong to a later time
+            for (int n = n0; n < n1; ++n) {
+                const double t = ws_steps[(size_t)n * 3], hs = ws_steps[(size_t)n * 3 + 1];
+                const double rat = fac_valid ? hs / h_f : 0.0;
+                if (!fac_valid || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
+                    refactor<S>(C, A, P, R, off, t, hs, sh);
+                    h_f = hs; fac_valid = true; since_fac = 0;
                 }
-            } else {
-                for (int i = threadIdx.x; i < S * N; i += NT) C.Z[i] = 0.0;
-            }
-            __syncthreads();
-            const double sc_err = atol + rtol * ymax;
-            const float fscale = (float)(h_f / hs);
-            bool conv = false, nonfinite = false;
-            float prev = 3.0e38f, theta = 0.f;
-            eta = powf(fmaxf(eta, 1e-7f), 0.8f);
-            for (int it = 0; it < A.tol.newton_max_iter; ++it) {
-                // F_j = A(t + c_j h)(y + Z_j) for all stages in one pass, FP64
-                for (int e = threadIdx.x; e < S * N; e += NT) C.yb[e] = C.y[e % N] + C.Z[e];
-                __syncthreads();
-                for (int e = threadIdx.x; e < S * N; e += NT) {
-                    const int j = e / N, i = e - j * N;
-                    C.F[e] = apply_row(i, C.yb + j * N, s_scj[j], C.diag, N, T);
+                stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
+                predict_stages<S>(C, false, sh);
+                float eta = 1.f;
+                const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_rep, eta, 0.02f, 4 * A.tol.newton_max_iter, sh);
+                // a stalled iteration whose last increment is already below the
+                // tolerance scale is as good as the forward's accepted stages
+                if (nr.nonfinite || (!nr.conv && !(nr.dmax <= (float)sc_rep))) {
+                    status = nr.nonfinite ? FP_STATUS_NONFINITE : FP_STATUS_NEWTON_FAIL;
+                    fail_phase = 2; fail_step = n;
+                    break;
                 }
-                __syncthreads();
-                // residual R = -Z + h a F (FP64) -> right-hand sides K R (FP32, block order)
-                for (int b = threadIdx.x; b < N; b += NT) {
-                    const int i = __ldg(C.glob + b);
-                    double fv[S];
-                    float Rk[S];
-#pragma unroll
-                    for (int j = 0; j < S; ++j) fv[j] = C.F[j * N + i];
-#pragma unroll
-                    for (int k = 0; k < S; ++k) {
-                        double acc = 0.0;
-#pragma unroll
-                        for (int j = 0; j < S; ++j) acc = fma(RAD<S>().a[k][j], fv[j], acc);
-                        Rk[k] = (float)fma(hs, acc, -C.Z[k * N + i]);
-                    }
-                    float q[S];
-#pragma unroll
-                    for (int k = 0; k < S; ++k) {
-                        float acc = 0.f;
-#pragma unroll
-                        for (int j = 0; j < S; ++j) acc = fmaf((float)RAD<S>().K[k][j], Rk[j], acc);
-                        q[k] = acc;
-                    }
-                    C.rr[b] = q[0];
-#pragma unroll
-                    for (int p = 0; p < NC; ++p) C.rc[p * N + b] = make_float2(q[1 + 2 * p], q[2 + 2 * p]);
-                }
-                __syncthreads();
-                {
-                    constexpr int GW = Groups<S>::GW;
-                    const int sys = w / GW, gw = w - sys * GW;
-                    if (sys == 0) group_solve<float, S, GW>(C, C.fr, C.rr, C.zr, gw, 1);
-                    else if (sys <= NC)
-                        group_solve<float2, S, GW>(C, C.fc + (size_t)(sys - 1) * C.ly.fsum, C.rc + (sys - 1) * N,
-                                                   C.zc + (sys - 1) * N, gw, 1 + sys);
-                }
-                __syncthreads();
-                // Z += T dW (h_f / h)
-                float dm = 0.f;
-                for (int b = threadIdx.x; b < N; b += NT) {
-                    const int i = __ldg(C.glob + b);
-                    float dW[S];
-                    dW[0] = fscale * C.zr[b];
-#pragma unroll
-                    for (int p = 0; p < NC; ++p) {
-                        float2 v = C.zc[p * N + b];
-                        dW[1 + 2 * p] = fscale * v.x;
-                        dW[2 + 2 * p] = fscale * v.y;
-                    }
-#pragma unroll
-                    for (int k = 0; k < S; ++k) {
-                        float dz = 0.f;
-#pragma unroll
-                        for (int j = 0; j < S; ++j) dz = fmaf((float)RAD<S>().T[k][j], dW[j], dz);
-                        C.Z[k * N + i] += (double)dz;
-                        dm = nanmax(dm, fabsf(dz));
-                    }
-                }
-                const float dmax = block_max(dm, s_red);
-                ++nit;
-                if (!(dmax <= 3.0e38f)) { nonfinite = true; break; }
-                if (it >= 1) {
-                    theta = dmax / prev;
-                    if (theta >= 0.99f) break;
-                    eta = theta / (1.f - theta);
-                }
-                if (eta * dmax <= kappa * (float)sc_err || dmax <= 1e-3f * (float)sc_err) { conv = true; break; }
-                prev = dmax;
-            }
-            if (nonfinite) { status = FP_STATUS_NONFINITE; break; }
-            if (!conv) {
-                ++nrej;
-                if (since_fac == 0 && hs <= 1e-6 * T_s) { status = FP_STATUS_NEWTON_FAIL; break; }
-                if (since_fac == 0) h = hs * 0.5;      // fresh factors did not converge: shrink the step
-                have_pred = false; force_refac = true; eta = 1.0f;
-                __syncthreads();
-                continue;
-            }
-            if (theta > 0.1f) force_refac = true;       // slow contraction: refresh the factors next step
-            // embedded error estimate, filtered through the real factor
-            for (int b = threadIdx.x; b < N; b += NT) {
-                const int i = __ldg(C.glob + b);
-                double ev = hs * RAD<S>().g0 * C.f0[i];
-#pragma unroll
-                for (int j = 0; j < S; ++j) ev = fma(RAD<S>().e[j], C.Z[j * N + i], ev);
-                C.rr[b] = (float)ev;
-            }
-            __syncthreads();
-            if (w < Groups<S>::GW) group_solve<float, S, Groups<S>::GW>(C, C.fr, C.rr, C.zr, w, 1);
-            __syncthreads();
-            float em = 0.f;
-            const float escale = (float)(RAD<S>().gam * h_f / hs);
-            for (int b = threadIdx.x; b < N; b += NT) em = nanmax(em, fabsf(escale * C.zr[b]));
-            const double en = (double)block_max(em, s_red) / sc_err;
-            if (!(en < 1e300)) { status = FP_STATUS_NONFINITE; break; }
-            const double fac = en > 0.0 ? 0.9 * (double)powf((float)en, -1.f / (S + 1)) : 4.0;
-            if (en <= 1.0) {
-                float ymx = 0.f;
+                ++since_fac;
+                double* zs = ws_Z + (size_t)(n - n0) * S * N;
+                for (int e = threadIdx.x; e < S * N; e += NT) zs[e] = C.Z[e];
                 for (int i = threadIdx.x; i < N; i += NT) {
                     C.y[i] += C.Z[(S - 1) * N + i];
-                    ymx = nanmax(ymx, fabsf((float)C.y[i]));
+                    ws_seg[(size_t)(n - n0 + 1) * N + i] = C.y[i];
                 }
-                ymax = block_max(ymx, s_red);
-                if (!(ymax <= 3.0e38)) { status = FP_STATUS_NONFINITE; break; }
-                ++nsteps; ++since_fac;
-                t = last ? tt : t + hs;
-                {   // f0 = A(t) y at the accepted point, for the next error estimate
-                    if (threadIdx.x == 0) {
-                        double Bn[3];
-                        field_nframe(A, R, off, t, Bn);
-                        s_scj[0] = make_scal(P, Bn);
+                __syncthreads();
+            }
+            if (status != FP_STATUS_OK) break;
+            fac_valid = false;
+            for (int n = n1 - 1; n >= n0; --n) {
+                const double t = ws_steps[(size_t)n * 3], hs = ws_steps[(size_t)n * 3 + 1];
+                const int js = (int)ws_steps[(size_t)n * 3 + 2];
+                // readout at t + hs if this step landed on a sample of the last period
+                if (js >= j0) {
+                    if (threadIdx.x < 3) s_g[threadIdx.x] = ws_g[(js - j0) * 3 + threadIdx.x];
+                    __syncthreads();
+                    double gl[3] = {s_g[0], s_g[1], s_g[2]};
+                    double grad_loc[4] = {0, 0, 0, 0};
+                    readout_adjoint<S>(C, A, P, in, R, off, t + hs, gl, ws_seg + (size_t)(n - n0 + 1) * N, grad_loc, sh);
+                    if (threadIdx.x == 0) for (int p = 0; p < 4; ++p) s_grad[p] += grad_loc[p];
+                    __syncthreads();
+                }
+                // state c_n and the replayed stage increments of step n
+                const double* zs = ws_Z + (size_t)(n - n0) * S * N;
+                for (int i = threadIdx.x; i < N; i += NT) C.y[i] = ws_seg[(size_t)(n - n0) * N + i];
+                for (int e = threadIdx.x; e < S * N; e += NT) C.Z[e] = zs[e];
+                __syncthreads();
+                const double rat = fac_valid ? hs / h_f : 0.0;
+                if (!fac_valid || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
+                    refactor<S>(C, A, P, R, off, t, hs, sh);
+                    h_f = hs; fac_valid = true; since_fac = 0;
+                }
+                ++since_fac;
+                stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
+                // transposed stage solve for zeta (in F)
+                const int ai = adjoint_stages<S>(C, T, hs, h_f, 4 * A.tol.newton_max_iter, sh);
+                if (ai < 0) {
+                    status = ai == -1 ? FP_STATUS_NONFINITE : FP_STATUS_NEWTON_FAIL;
+                    fail_phase = 3; fail_step = n;
+                    break;
+                }
+                // gradient: h sum_j xi_j^T (dA_j/dp) Y_j with xi_j = sum_i a_ij zeta_i, Y_j = c_n + Z_j
+                double gacc[4] = {0, 0, 0, 0};
+                for (int j = 0; j < S; ++j) {
+                    for (int i = threadIdx.x; i < N; i += NT) {
+                        double xv = 0.0;
+#pragma unroll
+                        for (int k = 0; k < S; ++k) xv = fma(RAD<S>().a[k][j], C.F[k * N + i], xv);
+                        C.yb[i] = xv;                                   // xi_j
+                        C.aw[i] = C.y[i] + C.Z[j * N + i];              // Y_j
                     }
                     __syncthreads();
-                    const AScal sn = s_scj[0];
-                    apply_A(C.y, C.f0, sn, C.diag, N, T);
-                    __syncthreads();
+                    double beta[10];
+                    bilinear(C.yb, C.aw, N, T, beta);
+                    block_sum10(beta, sh.dred);
+                    double Bl[3];
+                    lab_field(A, off, t + RAD<S>().c[j] * hs, Bl);
+                    DScal ds[4];
+                    dscal_all(A.mat, P, in.d, in.theta, in.phi, Bl, ds);
+                    for (int p = 0; p < 4; ++p) gacc[p] += hs * dot_dscal(ds[p], beta);
                 }
-                if (last) { write_sample(jn, tt); ++jn; }
-                double hn = hs * fmin(4.0, fmax(0.2, fac));
-                if (last && hs < h) hn = fac < 1.0 ? fmin(h, hn) : h;
-                // keep the factorised step when the controller asks for a small change
-                if (fac_valid && hn >= 0.9 * h_f && hn <= 1.2 * h_f) hn = fmax(h_f, hs);
-                h = fmin(hn, T_s);
-                h_old = hs;
-                have_pred = true;
-            } else {
-                ++nrej;
-                h = hs * fmax(0.1, fac);
-                have_pred = false;
+                if (threadIdx.x == 0) for (int p = 0; p < 4; ++p) s_grad[p] += gacc[p];
+                // lambda_n = sum_i zeta_i
+                for (int i = threadIdx.x; i < N; i += NT) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int k = 0; k < S; ++k) v += C.F[k * N + i];
+                    C.lam[i] = v;
+                }
+                __syncthreads();
             }
-            __syncthreads();
+        }
+        if (status == FP_STATUS_OK) {
+            // readout at t = 0 when the schedule samples it (and it lies in the last period)
+            if (sample_time(A.drv, 0) <= 0.0 && j0 == 0) {
+                if (threadIdx.x < 3) s_g[threadIdx.x] = ws_g[threadIdx.x];
+                for (int i = threadIdx.x; i < N; i += NT) C.y[i] = ws_ckpt[i];
+                __syncthreads();
+                double gl[3] = {s_g[0], s_g[1], s_g[2]};
+                double grad_loc[4] = {0, 0, 0, 0};
+                readout_adjoint<S>(C, A, P, in, R, off, 0.0, gl, C.y, grad_loc, sh);
+                if (threadIdx.x == 0) for (int p = 0; p < 4; ++p) s_grad[p] += grad_loc[p];
+                __syncthreads();
+            }
+            // initial state: lambda_0^T dc_0/dp by central differences of the projection
+            double Bl[3];
+            lab_field(A, off, 0.0, Bl);
+            for (int p = 0; p < 4; ++p) {
+                double val[2];
+                const double base = p == 0 ? in.K : p == 1 ? in.d : p == 2 ? in.theta : in.phi;
+                const double dp = p <= 1 ? 1e-5 * fmax(fabs(base), p == 0 ? 1.0 : 1e-9) : 1e-5;
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    const double v = base + (sgn == 0 ? dp : -dp);
+                    const double K = p == 0 ? v : in.K, d = p == 1 ? v : in.d;
+                    const double th = p == 2 ? v : in.theta, ph = p == 3 ? v : in.phi;
+                    const FpParams Pp = fp_derive(A.mat, K, d);
+                    double Rp[9], Bp[3];
+                    fp_rotation(th, ph, Rp);
+                    for (int r = 0; r < 3; ++r) Bp[r] = Rp[3 * r] * Bl[0] + Rp[3 * r + 1] * Bl[1] + Rp[3 * r + 2] * Bl[2];
+                    initial_state<S>(C, Pp, Bp, smem, C.yb);
+                    double part = 0.0;
+                    for (int i = threadIdx.x; i < N; i += NT) part = fma(C.lam[i], C.yb[i], part);
+                    double tmp[10] = {part, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+                    block_sum10(tmp, sh.dred);
+                    val[sgn] = tmp[0];
+                }
+                if (threadIdx.x == 0) s_grad[p] += (val[0] - val[1]) / (2.0 * dp);
+                __syncthreads();
+            }
         }
         if (threadIdx.x == 0) {
             A.status[inst] = status;
+            for (int p = 0; p < 4; ++p) G.grad[inst * 4 + p] = status == FP_STATUS_OK ? s_grad[p] : 0.0;
             if (A.stats) {
-                A.stats[inst * 4 + 0] = nsteps; A.stats[inst * 4 + 1] = nrej;
-                A.stats[inst * 4 + 2] = nit;    A.stats[inst * 4 + 3] = nfac;
+                A.stats[inst * 4 + 0] = fo.nsteps; A.stats[inst * 4 + 1] = fo.nrej;
+                A.stats[inst * 4 + 2] = fo.status != FP_STATUS_OK ? 1 : fail_phase;
+                A.stats[inst * 4 + 3] = fail_step;
             }
-        }
-        for (int e = jn * 3 + threadIdx.x; e < A.S_out * 3; e += NT) {
-            if (A.m_out) A.m_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
-            if (A.dmdt_out) A.dmdt_out[(size_t)inst * A.S_out * 3 + e] = 0.0;
         }
         __syncthreads();
     }
@@ -910,6 +1509,55 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
         e = cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return FP_ECUDA;
         fp_solve_kernel<3><<<grid, NT, sm, st>>>(A);
+    }
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
+}
+
+size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec) {
+    const size_t Nmax = (size_t)(L_max + 1) * (L_max + 1);
+    return (size_t)max_rec * 3 + (size_t)(max_rec / FP_CKPT + 1) * Nmax + (size_t)(FP_CKPT + 1) * Nmax +
+           (size_t)S_p * 3 + (size_t)FP_CKPT * stages * Nmax;
+}
+
+int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
+                      const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, int k_max,
+                      const double* channels, int C, const double* d_dJ, const double* d_tw, double* d_grad,
+                      int* d_status, int* d_stats, double* d_work, int max_rec, int grid, cudaStream_t st) {
+    GArgs G;
+    KArgs& A = G.A;
+    A.tab = *tab;
+    A.blk = *blk;
+    A.mat = *mat;
+    A.drv = *drv;
+    A.tol = *tol;
+    A.inst = d_inst;
+    A.n = n;
+    A.m_out = nullptr;
+    A.dmdt_out = nullptr;
+    A.status = d_status;
+    A.stats = d_stats;
+    A.S_out = drv->output_periods * drv->samples_per_period;
+    A.L_launch = L_launch;
+    G.dJ = d_dJ;
+    G.grad = d_grad;
+    G.tw = d_tw;
+    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < 3; ++k) G.ch[c][k] = c < C ? channels[3 * c + k] : 0.0;
+    G.C = C;
+    G.K = k_max;
+    G.work = d_work;
+    G.max_rec = max_rec;
+    G.work_per_cta = fp_adjoint_work_doubles_per_cta(stages, L_launch, drv->samples_per_period, max_rec);
+    size_t sm = fp_adjoint_smem_bytes(stages, L_launch);
+    cudaError_t e;
+    if (stages == 5) {
+        e = cudaFuncSetAttribute(fp_adjoint_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return FP_ECUDA;
+        fp_adjoint_kernel<5><<<grid, NT, sm, st>>>(G);
+    } else {
+        e = cudaFuncSetAttribute(fp_adjoint_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return FP_ECUDA;
+        fp_adjoint_kernel<3><<<grid, NT, sm, st>>>(G);
     }
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
 }

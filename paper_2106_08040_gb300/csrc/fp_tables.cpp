@@ -289,8 +289,9 @@ int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out) {
     out->up_g = (unsigned char*)std::calloc((size_t)N * FP_NLT, 1);
     out->up_cf = (float*)std::calloc((size_t)N * FP_NLT, sizeof(float));
     out->dnT = (unsigned char*)std::malloc((size_t)N * FP_NLT);
+    out->upT = (unsigned char*)std::malloc((size_t)N * FP_NLT);
     if (!out->glob || !out->sb_k || !out->sb_g || !out->sb_cf || !out->dn_k || !out->dn_g || !out->dn_cf ||
-        !out->up_k || !out->up_g || !out->up_cf || !out->dnT) {
+        !out->up_k || !out->up_g || !out->up_cf || !out->dnT || !out->upT) {
         fp_free_blocks(out);
         return FP_ENOMEM;
     }
@@ -298,6 +299,7 @@ int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out) {
     std::memset(out->dn_k, 255, (size_t)N * FP_NLT);
     std::memset(out->up_k, 255, (size_t)N * FP_NLT);
     std::memset(out->dnT, 255, (size_t)N * FP_NLT);
+    std::memset(out->upT, 255, (size_t)N * FP_NLT);
     std::vector<int> boff(L + 2, 0), blk_of(N), loc_of(N), brow(N);
     for (int mu = 0; mu <= L; ++mu) boff[mu + 1] = boff[mu] + nblock(mu, L);
     for (int g = 0; g < N; ++g) {
@@ -332,6 +334,32 @@ int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out) {
             if (nsb > FP_NSB || ndn > FP_NLT || nup > FP_NLT) { fp_free_blocks(out); return FP_EINVAL; }
         }
     }
+    // make the dn/up patterns mutually symmetric: row (0,0) of A vanishes (mass
+    // conservation) while its column does not, so add explicit zero couplings
+    // where only the reverse direction exists (the transposed solve needs them)
+    auto add_if_missing = [&](unsigned char* kl, unsigned char* gl, float* cl, int row, int kloc) -> bool {
+        for (int q = 0; q < FP_NLT; ++q)
+            if (kl[row * FP_NLT + q] == kloc) return true;
+        for (int q = 0; q < FP_NLT; ++q)
+            if (kl[row * FP_NLT + q] == 255) {
+                kl[row * FP_NLT + q] = (unsigned char)kloc; gl[row * FP_NLT + q] = 0; cl[row * FP_NLT + q] = 0.f;
+                return true;
+            }
+        return false;
+    };
+    for (int b = 0; b < N; ++b) {
+        int g = out->glob[b], mu = blk_of[g];
+        for (int p = 0; p < FP_NLT; ++p) {
+            int kd = out->dn_k[b * FP_NLT + p];
+            if (kd != 255 && !add_if_missing(out->up_k, out->up_g, out->up_cf, boff[mu - 1] + kd, loc_of[g])) {
+                fp_free_blocks(out); return FP_EINVAL;
+            }
+            int ku = out->up_k[b * FP_NLT + p];
+            if (ku != 255 && !add_if_missing(out->dn_k, out->dn_g, out->dn_cf, boff[mu + 1] + ku, loc_of[g])) {
+                fp_free_blocks(out); return FP_EINVAL;
+            }
+        }
+    }
     // back pointers: for dn partner p of row b, the slot of the partner's up list that points to b
     for (int b = 0; b < N; ++b) {
         int g = out->glob[b], mu = blk_of[g];
@@ -342,13 +370,34 @@ int fp_build_blocks(const FpTablesHost* t, int L, FpBlkHost* out) {
             for (int q = 0; q < FP_NLT; ++q)
                 if (out->up_k[bp * FP_NLT + q] == loc_of[g]) { out->dnT[b * FP_NLT + p] = (unsigned char)q; break; }
         }
+        for (int p = 0; p < FP_NLT; ++p) {
+            int ku = out->up_k[b * FP_NLT + p];
+            if (ku == 255) continue;
+            int bp = boff[mu + 1] + ku;
+            for (int q = 0; q < FP_NLT; ++q)
+                if (out->dn_k[bp * FP_NLT + q] == loc_of[g]) { out->upT[b * FP_NLT + p] = (unsigned char)q; break; }
+        }
     }
+    return FP_OK;
+}
+
+int fp_build_columns(const FpTablesHost* t, FpPair* out) {
+    const int N = t->N;
+    std::vector<int> cnt(N, 0);
+    for (int i = 0; i < N * FP_NCT; ++i) out[i] = FpPair{-1, 0};
+    for (int r = 0; r < N; ++r)
+        for (int k = 0; k < FP_NSLOT; ++k) {
+            int j = t->src[r * FP_NSLOT + k];
+            if (j < 0 || j >= N) continue;
+            if (cnt[j] >= FP_NCT) return FP_EINVAL;
+            out[j * FP_NCT + cnt[j]++] = FpPair{r, k};
+        }
     return FP_OK;
 }
 
 void fp_free_blocks(FpBlkHost* b) {
     std::free(b->glob); std::free(b->sb_k); std::free(b->sb_g); std::free(b->sb_cf);
     std::free(b->dn_k); std::free(b->dn_g); std::free(b->dn_cf);
-    std::free(b->up_k); std::free(b->up_g); std::free(b->up_cf); std::free(b->dnT);
+    std::free(b->up_k); std::free(b->up_g); std::free(b->up_cf); std::free(b->dnT); std::free(b->upT);
     std::memset(b, 0, sizeof(*b));
 }

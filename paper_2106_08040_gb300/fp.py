@@ -151,6 +151,86 @@ def fp_signal(ctx: Context, d_dmdt, n: int, k_max: int, channels, d_phihat, stre
                                _stream_ptr(stream)), "fp_signal")
 
 
+def fp_grad_workspace_bytes(ctx: Context, n: int) -> int:
+    v = _lib.lib().fp_grad_workspace_bytes(ctx.handle, int(n))
+    if v < 0:
+        check(int(v), "fp_grad_workspace_bytes")
+    return int(v)
+
+
+def fp_grad(ctx: Context, d_inst, n: int, k_max: int, channels, d_dJ, d_grad, d_status, d_work, d_stats=None,
+            stream=None):
+    """Discrete adjoint: d_grad[n,4] = dJ/d(K, d, theta, phi) given dJ/dphi_hat."""
+    ch = np.ascontiguousarray(np.asarray(channels, dtype=np.float64).reshape(-1, 3))
+    nbytes = d_work.numel() * d_work.element_size()
+    check(_lib.lib().fp_grad(ctx.handle, _ptr(d_inst), int(n), int(k_max),
+                             ch.ctypes.data_as(C.POINTER(C.c_double)), int(ch.shape[0]), _ptr(d_dJ), _ptr(d_grad),
+                             _ptr(d_status), _ptr(d_stats), _ptr(d_work), C.c_ulonglong(nbytes),
+                             _stream_ptr(stream)), "fp_grad")
+
+
+def pack_instances(h_off, params, L, device):
+    """Device instance records from tensors: h_off [n,3], params [n,4] =
+    (K, d, theta, phi), L int.  Float64 columns + (L, flags) int32 pair."""
+    import torch
+    n = params.shape[0]
+    Lf = torch.zeros((n, 2), dtype=torch.int32, device=device)
+    Lf[:, 0] = L
+    cols = torch.cat([h_off.to(device, torch.float64), params[:, 2:4].to(device, torch.float64),
+                      params[:, 0:2].to(device, torch.float64), Lf.view(torch.float64)], dim=1)
+    return cols.contiguous().view(torch.uint8).reshape(-1)
+
+
+def _autograd_function():
+    import torch
+
+    class PhiHat(torch.autograd.Function):
+        """phi_hat [n, C, k_max+1, 2] of the batched solve as a function of the
+        per-instance parameters (K, d, theta, phi); backward = fp_grad."""
+
+        @staticmethod
+        def forward(ctx_, params, h_off, fpctx, L, k_max, channels):
+            dev = params.device
+            n = params.shape[0]
+            S = fpctx.num_samples()
+            d_inst = pack_instances(h_off, params.detach(), L, dev)
+            dm = torch.empty((n, S, 3), dtype=torch.float64, device=dev)
+            st = torch.empty((n,), dtype=torch.int32, device=dev)
+            fp_solve_batch(fpctx, d_inst, n, None, dm, st, None)
+            ch = np.asarray(channels, dtype=np.float64).reshape(-1, 3)
+            out = torch.empty((n, ch.shape[0], k_max + 1, 2), dtype=torch.float64, device=dev)
+            fp_signal(fpctx, dm, n, k_max, ch, out)
+            ctx_.save_for_backward(params.detach(), h_off)
+            ctx_.fpctx, ctx_.L, ctx_.k_max, ctx_.ch = fpctx, L, k_max, ch
+            ctx_.status = st
+            return out
+
+        @staticmethod
+        def backward(ctx_, g):
+            params, h_off = ctx_.saved_tensors
+            dev = params.device
+            n = params.shape[0]
+            d_inst = pack_instances(h_off, params, ctx_.L, dev)
+            grad = torch.empty((n, 4), dtype=torch.float64, device=dev)
+            st = torch.empty((n,), dtype=torch.int32, device=dev)
+            work = torch.empty(fp_grad_workspace_bytes(ctx_.fpctx, n), dtype=torch.uint8, device=dev)
+            fp_grad(ctx_.fpctx, d_inst, n, ctx_.k_max, ctx_.ch, g.contiguous().to(torch.float64), grad, st, work)
+            return grad.to(params.dtype), None, None, None, None, None
+
+    return PhiHat
+
+
+_PHIHAT = None
+
+
+def phi_hat(params, h_off, fpctx, L, k_max, channels):
+    """Differentiable phi_hat (torch.autograd) of the batched solve."""
+    global _PHIHAT
+    if _PHIHAT is None:
+        _PHIHAT = _autograd_function()
+    return _PHIHAT.apply(params, h_off, fpctx, L, k_max, channels)
+
+
 def fp_operator_dense(material: Material, L: int, K: float, d: float, B_nframe):
     """Dense easy-axis-frame Galerkin matrix (host only, no GPU)."""
     N = (L + 1) ** 2
