@@ -184,6 +184,31 @@ int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
             double* d_grad, int* d_status, int* d_stats, void* d_work,
             unsigned long long work_bytes, void* stream);
 
+/* The paper has no counterpart: this is a library convenience.
+ * fp_grad without a workspace argument, for callers that may not allocate
+ * device memory when they call: a host program that gives this library a
+ * fixed device-memory footprint and forbids further cudaMalloc (a plugin inside
+ * another runtime, a long-running service that must not grow or fragment its
+ * memory), or one that cannot size and keep a workspace of its own.  It
+ * allocates nothing: the scratch is a static device array of
+ * FP_GRAD_NOALLOC_SCRATCH_BYTES compiled into libfp.so, held by every GPU that
+ * loads the library until the process exits.  Arguments, outputs, statuses and
+ * stats as in fp_grad.  The scratch bounds how many instances run at once
+ * (fewer CTAs, each taking several instances in turn), not n; if a single
+ * instance needs more than the array (fp_grad_workspace_bytes(ctx, 1) >
+ * FP_GRAD_NOALLOC_SCRATCH_BYTES; lower fp_tol.max_steps or L_max) the call
+ * returns FP_EINVAL with the sizes in fp_last_error() and launches nothing.
+ * The current device must be the context's.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array and overwrites what the previous call left there (nothing in it needs
+ * to start at zero): calls whose launches may overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+#define FP_GRAD_NOALLOC_SCRATCH_BYTES (32ull << 20)
+int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
+                    const double* h_channels, int C, const double* d_dJ_dphihat,
+                    double* d_grad, int* d_status, int* d_stats, void* stream);
+
 /* Diagnostic (host only, no GPU needed): dense Galerkin matrix A of
  * dc/dt = A c (Eq. FP-general tested against the real SH basis) for one
  * instance in the EASY-AXIS frame (n = z), with the field B_nframe [T] already

@@ -13,7 +13,7 @@ FP_OK, FP_EINVAL, FP_ECUDA, FP_ENOMEM, FP_EUNSUPPORTED = 0, -1, -2, -3, -4
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT"}
 
 EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_solve_batch",
-            "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_operator_dense", "fp_peak_fp64",
+            "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_grad_noalloc", "fp_operator_dense", "fp_peak_fp64",
             "fp_status_str", "fp_last_error"]
 
 
@@ -71,6 +71,8 @@ def lib():
     L.fp_grad_workspace_bytes.restype = C.c_longlong
     L.fp_grad.argtypes = [vp, vp, i, i, C.POINTER(d), i, vp, vp, vp, vp, vp, C.c_ulonglong, vp]
     L.fp_grad.restype = i
+    L.fp_grad_noalloc.argtypes = [vp, vp, i, i, C.POINTER(d), i, vp, vp, vp, vp, vp]
+    L.fp_grad_noalloc.restype = i
     L.fp_peak_fp64.argtypes = [C.POINTER(d)]
     L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]

@@ -349,3 +349,86 @@ extern "C" int fp_operator_dense(const fp_material* mat, const fp_instance* h_in
     fp_free_tables(&tb);
     return FP_OK;
 }
+
+// ------------------------------------------------ fp_grad without allocation ----
+// fp_grad_noalloc runs the adjoint kernel of fp_grad on a fixed scratch buffer
+// compiled into this library instead of a caller-supplied workspace.  It is for
+// callers that may not allocate device memory at call time: a host program that
+// gives this library a fixed device-memory footprint and forbids further
+// cudaMalloc (a plugin inside another runtime, a service that must not grow
+// or fragment its memory while it runs), or one that cannot size and keep a
+// workspace of its own.  The buffer is a static __device__ array, so every GPU
+// that loads the library holds FP_GRAD_NOALLOC_SCRATCH_BYTES until the process
+// exits.  Host code cannot use the array's name as a device address; the
+// device address is looked up once per device with cudaGetSymbolAddress.
+#include <mutex>
+
+static __device__ __align__(256) double g_fp_grad_scratch[FP_GRAD_NOALLOC_SCRATCH_BYTES / sizeof(double)];
+
+#define FP_NOALLOC_MAX_DEVICES 64
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_scratch[FP_NOALLOC_MAX_DEVICES];   // device address per device, set on first use
+
+// Device address of the scratch array on the current device `dev` (which the
+// caller has checked is current); the first call per device does the lookup.
+static int noalloc_scratch(int dev, double** out) {
+    if (dev < 0 || dev >= FP_NOALLOC_MAX_DEVICES)
+        return fail(FP_EUNSUPPORTED, "fp_grad_noalloc: device %d beyond %d", dev, FP_NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_scratch[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_fp_grad_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(FP_ECUDA, "fp_grad_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_scratch[dev] = (double*)p;
+    }
+    *out = g_noalloc_scratch[dev];
+    return FP_OK;
+}
+
+extern "C" int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max, const double* h_channels,
+                               int C, const double* d_dJ_dphihat, double* d_grad, int* d_status, int* d_stats,
+                               void* stream) {
+    if (!ctx) return fail(FP_EINVAL, "fp_grad_noalloc: NULL ctx");
+    if (n < 0) return fail(FP_EINVAL, "fp_grad_noalloc: n < 0");
+    if (n == 0) return FP_OK;
+    if (!d_inst || !d_dJ_dphihat || !d_grad || !d_status || !h_channels)
+        return fail(FP_EINVAL, "fp_grad_noalloc: NULL buffer");
+    if (k_max < 0 || k_max >= ctx->drv.samples_per_period)
+        return fail(FP_EINVAL, "fp_grad_noalloc: k_max=%d", k_max);
+    if (C < 1 || C > 4) return fail(FP_EINVAL, "fp_grad_noalloc: C=%d outside [1, 4]", C);
+    // one CTA works through its instances one after another in its own slice
+    // of the buffer, so the buffer bounds the number of CTAs, not n
+    const unsigned long long per_cta =
+        8ull * fp_adjoint_work_doubles_per_cta(ctx->tol.stages, ctx->L_max, ctx->drv.samples_per_period,
+                                               ctx->tol.max_steps);
+    const unsigned long long fit = FP_GRAD_NOALLOC_SCRATCH_BYTES / per_cta;
+    if (fit == 0)
+        return fail(FP_EINVAL,
+                    "fp_grad_noalloc: one instance needs %llu bytes of scratch (L_max=%d, max_steps=%d), the fixed "
+                    "buffer holds %llu; lower fp_tol.max_steps or L_max, or use fp_grad with a workspace",
+                    per_cta, ctx->L_max, ctx->tol.max_steps, (unsigned long long)FP_GRAD_NOALLOC_SCRATCH_BYTES);
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ctx->device)
+        return fail(FP_EINVAL, "fp_grad_noalloc: current device %d, context lives on device %d", dev, ctx->device);
+    size_t sm = fp_adjoint_smem_bytes(ctx->tol.stages, ctx->L_max);
+    int max_sm = 0;
+    cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if ((int)sm > max_sm)
+        return fail(FP_EUNSUPPORTED, "fp_grad_noalloc: %zu bytes of shared memory needed, %d available", sm, max_sm);
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(dev, &scratch);
+    if (rc != FP_OK) return rc;
+    // every scratch word the kernel reads it has written earlier in the same
+    // launch (recorded steps, checkpoints, segment states and stages, readout
+    // cotangents), so what an earlier call left there needs no clearing
+    int grid = n < ctx->num_sms ? n : ctx->num_sms;
+    if ((unsigned long long)grid > fit) grid = (int)fit;
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT};
+    rc = fp_launch_adjoint(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
+                           k_max, h_channels, C, d_dJ_dphihat, ctx->d_tw, d_grad, d_status, d_stats, scratch,
+                           ctx->tol.max_steps, grid, (cudaStream_t)stream);
+    if (rc != FP_OK) return fail(rc, "fp_grad_noalloc: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return FP_OK;
+}

@@ -169,6 +169,19 @@ def fp_grad(ctx: Context, d_inst, n: int, k_max: int, channels, d_dJ, d_grad, d_
                              _stream_ptr(stream)), "fp_grad")
 
 
+def fp_grad_noalloc(ctx: Context, d_inst, n: int, k_max: int, channels, d_dJ, d_grad, d_status, d_stats=None,
+                    stream=None):
+    """fp_grad on the library's fixed device scratch array: no workspace and
+    no device allocation, for callers that may not allocate device memory when
+    they call.  Calls whose launches may overlap on the GPU share the array and
+    race; the first call on a device should come before any stream capture."""
+    ch = np.ascontiguousarray(np.asarray(channels, dtype=np.float64).reshape(-1, 3))
+    check(_lib.lib().fp_grad_noalloc(ctx.handle, _ptr(d_inst), int(n), int(k_max),
+                                     ch.ctypes.data_as(C.POINTER(C.c_double)), int(ch.shape[0]), _ptr(d_dJ),
+                                     _ptr(d_grad), _ptr(d_status), _ptr(d_stats), _stream_ptr(stream)),
+          "fp_grad_noalloc")
+
+
 def pack_instances(h_off, params, L, device):
     """Device instance records from tensors: h_off [n,3], params [n,4] =
     (K, d, theta, phi), L int.  Float64 columns + (L, flags) int32 pair."""
