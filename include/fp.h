@@ -209,6 +209,74 @@ int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
                     const double* h_channels, int C, const double* d_dJ_dphihat,
                     double* d_grad, int* d_status, int* d_stats, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Harmonic surrogate: a multilayer perceptron mapping one instance
+ * (offset field B_off [T] (3), easy-axis theta, phi [rad], ln K, ln d) to the
+ * leading harmonics of its normalised signal phi_hat (Sec. 2.2, model M1),
+ * FP_SUR_OUT = 2 channels x 200 complex harmonics k = 1..200, stored
+ * [channel][k-1][re, im].  The paper has no surrogate; the Fokker-Planck solve
+ * (fp_solve_batch + fp_signal) produces its training data and judges its error.
+ * Layers l = 0..4: z_l = W_l x_l + b_l with x_0 the normalised, zero-padded
+ * input (64 wide), x_{l+1} = gelu(z_l) (exact erf form) for l < 4 and the
+ * output y = z_4 * out_scale + out_shift.  BF16 operands, FP32 accumulation on
+ * the tensor cores (tcgen05, TMEM accumulators, TMA-fed shared memory).
+ * Weight layouts (row-major, bf16): W_l [N_l][K_l] with K = (64, 512, 512,
+ * 512, 512), N = (512, 512, 512, 512, 800); columns 7..63 of W_0 must be 0.
+ * ------------------------------------------------------------------------- */
+#define FP_SUR_IN 7
+#define FP_SUR_KIN 64
+#define FP_SUR_HIDDEN 512
+#define FP_SUR_LAYERS 5
+#define FP_SUR_OUT 800
+
+typedef struct {
+    const void* W[FP_SUR_LAYERS];     /* bf16 [N_l][K_l] */
+    const float* b[FP_SUR_LAYERS];    /* f32 [N_l] */
+    const float* in_shift;            /* f32 [7]: x_norm = (x - in_shift) * in_scale */
+    const float* in_scale;            /* f32 [7] */
+    const float* out_shift;           /* f32 [800] */
+    const float* out_scale;           /* f32 [800] */
+} fp_surrogate;
+
+/* Training state: the inference view plus what the optimiser keeps. */
+typedef struct {
+    fp_surrogate net;                 /* net.W are refreshed from Wm by fp_surrogate_adam */
+    void* WT[FP_SUR_LAYERS];          /* bf16 [K_l][N_l], transposed copies (backward) */
+    float* Wm[FP_SUR_LAYERS];         /* f32 master weights [N_l][K_l] */
+    float* bm[FP_SUR_LAYERS];         /* f32 biases (the buffers net.b points to) */
+    float* mW[FP_SUR_LAYERS];         /* Adam first / second moments, f32, like Wm */
+    float* vW[FP_SUR_LAYERS];
+    float* mb[FP_SUR_LAYERS];         /* like bm */
+    float* vb[FP_SUR_LAYERS];
+} fp_surrogate_train;
+
+/* Device workspace (bytes) for q queries: inference (training = 0) or one
+ * gradient evaluation (training = 1; q must then be a multiple of 8). */
+long long fp_surrogate_workspace_bytes(int q, int training);
+
+/* Surrogate inference: d_x [q][7] f32 -> d_y [q][800] f32.  d_err (device
+ * int, required) is OR-ed with a nonzero code if a kernel wait timed out
+ * (never expected; the outputs are then undefined).  d_work: workspace of
+ * fp_surrogate_workspace_bytes(q, 0) bytes, contents undefined on return.
+ * Asynchronous. */
+int fp_surrogate_infer(const fp_surrogate* net, const float* d_x, int q, float* d_y, void* d_work,
+                       unsigned long long work_bytes, int* d_err, void* stream);
+
+/* Loss and gradients of one batch: loss = sum over queries and outputs of
+ * (z_4 - (y - out_shift)/out_scale)^2, written to *d_loss (f32, overwritten);
+ * d_gW[l] f32 [N_l][K_l] and d_gb[l] f32 [N_l] receive the gradients of
+ * loss / (q * 800) (mean squared error in normalised output units).  Uses the
+ * bf16 weights t->net.W, t->WT and biases.  Asynchronous. */
+int fp_surrogate_grad(const fp_surrogate_train* t, const float* d_x, const float* d_y, int q, float* d_loss,
+                      float* const* d_gW, float* const* d_gb, void* d_work, unsigned long long work_bytes,
+                      int* d_err, void* stream);
+
+/* Adam step (bias-corrected, step >= 1) on the master weights and biases from
+ * the gradients, then refresh the bf16 copies t->net.W and t->WT.  step = 0
+ * only refreshes the copies (after initialising Wm).  Asynchronous. */
+int fp_surrogate_adam(const fp_surrogate_train* t, float* const* d_gW, float* const* d_gb, float lr, float beta1,
+                      float beta2, float eps, int step, void* stream);
+
 /* Diagnostic (host only, no GPU needed): dense Galerkin matrix A of
  * dc/dt = A c (Eq. FP-general tested against the real SH basis) for one
  * instance in the EASY-AXIS frame (n = z), with the field B_nframe [T] already

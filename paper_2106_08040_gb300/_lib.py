@@ -13,7 +13,8 @@ FP_OK, FP_EINVAL, FP_ECUDA, FP_ENOMEM, FP_EUNSUPPORTED = 0, -1, -2, -3, -4
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT"}
 
 EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_solve_batch",
-            "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_grad_noalloc", "fp_operator_dense", "fp_peak_fp64",
+            "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_grad_noalloc", "fp_surrogate_workspace_bytes", "fp_surrogate_infer",
+            "fp_surrogate_grad", "fp_surrogate_adam", "fp_operator_dense", "fp_peak_fp64",
             "fp_status_str", "fp_last_error"]
 
 
@@ -36,6 +37,20 @@ class fp_tol(C.Structure):
 class fp_instance(C.Structure):
     _fields_ = [("h_off", C.c_double * 3), ("theta", C.c_double), ("phi", C.c_double),
                 ("K", C.c_double), ("d", C.c_double), ("L", C.c_int), ("flags", C.c_int)]
+
+
+SUR_LAYERS = 5
+
+
+class fp_surrogate(C.Structure):
+    _fields_ = [("W", C.c_void_p * SUR_LAYERS), ("b", C.c_void_p * SUR_LAYERS), ("in_shift", C.c_void_p),
+                ("in_scale", C.c_void_p), ("out_shift", C.c_void_p), ("out_scale", C.c_void_p)]
+
+
+class fp_surrogate_train(C.Structure):
+    _fields_ = [("net", fp_surrogate), ("WT", C.c_void_p * SUR_LAYERS), ("Wm", C.c_void_p * SUR_LAYERS),
+                ("bm", C.c_void_p * SUR_LAYERS), ("mW", C.c_void_p * SUR_LAYERS), ("vW", C.c_void_p * SUR_LAYERS),
+                ("mb", C.c_void_p * SUR_LAYERS), ("vb", C.c_void_p * SUR_LAYERS)]
 
 
 assert C.sizeof(fp_instance) == 64
@@ -73,6 +88,16 @@ def lib():
     L.fp_grad.restype = i
     L.fp_grad_noalloc.argtypes = [vp, vp, i, i, C.POINTER(d), i, vp, vp, vp, vp, vp]
     L.fp_grad_noalloc.restype = i
+    f = C.c_float
+    L.fp_surrogate_workspace_bytes.argtypes = [i, i]
+    L.fp_surrogate_workspace_bytes.restype = C.c_longlong
+    L.fp_surrogate_infer.argtypes = [C.POINTER(fp_surrogate), vp, i, vp, vp, C.c_ulonglong, vp, vp]
+    L.fp_surrogate_infer.restype = i
+    L.fp_surrogate_grad.argtypes = [C.POINTER(fp_surrogate_train), vp, vp, i, vp, C.POINTER(vp), C.POINTER(vp), vp,
+                                    C.c_ulonglong, vp, vp]
+    L.fp_surrogate_grad.restype = i
+    L.fp_surrogate_adam.argtypes = [C.POINTER(fp_surrogate_train), C.POINTER(vp), C.POINTER(vp), f, f, f, f, i, vp]
+    L.fp_surrogate_adam.restype = i
     L.fp_peak_fp64.argtypes = [C.POINTER(d)]
     L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]

@@ -50,6 +50,15 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+// error reporting for the other translation units (fp_mlp.cu)
+int fp_fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
 #define CUDA_TRY(call)                                                                 \
     do {                                                                               \
         cudaError_t e_ = (call);                                                       \
