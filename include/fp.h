@@ -62,6 +62,8 @@ extern "C" {
 #define FP_STATUS_NONFINITE      3  /* NaN/Inf in the state                      */
 #define FP_STATUS_NEWTON_FAIL    4  /* Newton iteration failed at the minimum step */
 #define FP_STATUS_BAD_INPUT      5  /* instance parameters out of range (L, K, d) */
+#define FP_STATUS_UNRESOLVED     6  /* |<m>| > 1 at a sample: the truncated operator at this L
+                                       is not dissipative for the instance (raise L) */
 
 /* Material of Sec. 2.1 / 2.4.1: saturation magnetisation Ms [A/m], Gilbert
  * damping alpha, gyromagnetic ratio gamma [rad/(s T)], temperature T_B [K]. */
@@ -153,6 +155,42 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n,
  * k = 0..k_max (k_max < S_p).  Output d_phihat [n][C][k_max+1][2] (re, im), FP64. */
 int fp_signal(fp_ctx* ctx, const double* d_dmdt, int n, int k_max,
               const double* h_channels, int C, double* d_phihat, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Uneven sweeps: tens of thousands of instances of different truncation degree
+ * L and stiffness in one submission (the instances are independent, Sec. 2.1,
+ * last paragraph; the parameter sweeps of Sec. 2.4.1).  fp_sweep_plan groups
+ * the host copy of the instances into buckets of equal launch degree (L rounded
+ * up to a multiple of bucket_width, at most the context's L_max), orders the
+ * buckets by decreasing L and each bucket by decreasing estimated cost
+ * (sigma + b_T |B|max), and allocates the device order array and work
+ * counters (the only allocations; plan before any stream capture).
+ * fp_sweep_run solves the instances d_inst (device copy of the same records,
+ * same order) into the layouts of fp_solve_batch: one persistent launch per
+ * bucket whose CTAs take instances from a work counter, the buckets forked
+ * onto side streams and joined; the whole submission is captured into a CUDA
+ * graph on the first run and replayed while (d_inst, d_m, d_dmdt, d_status,
+ * d_stats, stream) stay the same.  stream must not be the legacy default
+ * stream (it cannot be captured).  fp_sweep_autotune times, per bucket, a
+ * strided sample of `sample` instances under each candidate (Radau stages 3
+ * or 5, refactorisation every 8 or 16 steps) and keeps the fastest candidate
+ * whose sample converged; it synchronises the stream and overwrites the
+ * sampled instances' outputs.  A plan borrows ctx, which must outlive it.
+ * ------------------------------------------------------------------------- */
+typedef struct fp_sweep fp_sweep;
+
+int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_width, fp_sweep** out);
+int fp_sweep_run(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_dmdt, int* d_status,
+                 int* d_stats, void* stream);
+int fp_sweep_autotune(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_dmdt, int* d_status,
+                      int sample, void* stream);
+/* Buckets of a plan: their count, and per bucket (arrays of at least
+ * FP_L_MAX_ANY entries, each may be NULL) launch degree, instance count,
+ * stages, refactorisation interval and the autotuned sample time [ms]. */
+#define FP_L_MAX_ANY 64
+int fp_sweep_info(const fp_sweep* sw, int* n_buckets, int* h_L, int* h_count, int* h_stages, int* h_refactor,
+                  float* h_tuned_ms);
+int fp_sweep_destroy(fp_sweep* sw);
 
 /* Device workspace (bytes) that fp_grad needs for n instances: per CTA of the
  * persistent launch, the recorded step sequence (fp_tol.max_steps steps), one

@@ -10,11 +10,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfp.so")
 
 FP_OK, FP_EINVAL, FP_ECUDA, FP_ENOMEM, FP_EUNSUPPORTED = 0, -1, -2, -3, -4
-STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT"}
+STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT",
+          6: "UNRESOLVED"}
 
 EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_solve_batch",
             "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_grad_noalloc", "fp_surrogate_workspace_bytes", "fp_surrogate_infer",
-            "fp_surrogate_grad", "fp_surrogate_adam", "fp_operator_dense", "fp_peak_fp64",
+            "fp_surrogate_grad", "fp_surrogate_adam", "fp_sweep_plan", "fp_sweep_run",
+            "fp_sweep_autotune", "fp_sweep_info", "fp_sweep_destroy", "fp_operator_dense", "fp_peak_fp64",
             "fp_status_str", "fp_last_error"]
 
 
@@ -98,6 +100,17 @@ def lib():
     L.fp_surrogate_grad.restype = i
     L.fp_surrogate_adam.argtypes = [C.POINTER(fp_surrogate_train), C.POINTER(vp), C.POINTER(vp), f, f, f, f, i, vp]
     L.fp_surrogate_adam.restype = i
+    L.fp_sweep_plan.argtypes = [vp, vp, i, i, C.POINTER(vp)]
+    L.fp_sweep_plan.restype = i
+    L.fp_sweep_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.fp_sweep_run.restype = i
+    L.fp_sweep_autotune.argtypes = [vp, vp, vp, vp, vp, i, vp]
+    L.fp_sweep_autotune.restype = i
+    L.fp_sweep_info.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i),
+                                C.POINTER(f)]
+    L.fp_sweep_info.restype = i
+    L.fp_sweep_destroy.argtypes = [vp]
+    L.fp_sweep_destroy.restype = i
     L.fp_peak_fp64.argtypes = [C.POINTER(d)]
     L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]

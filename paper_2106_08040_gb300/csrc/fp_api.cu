@@ -10,36 +10,6 @@
 #include <vector>
 #include "fp_internal.h"
 
-size_t fp_solver_smem_bytes(int stages, int L);
-int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
-                    const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
-                    int* d_status, int* d_stats, int grid, cudaStream_t st);
-int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw);
-size_t fp_adjoint_smem_bytes(int stages, int L);
-size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec);
-int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
-                      const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, int k_max,
-                      const double* channels, int C, const double* d_dJ, const double* d_tw, double* d_grad,
-                      int* d_status, int* d_stats, double* d_work, int max_rec, int grid, cudaStream_t st);
-
-struct fp_ctx {
-    fp_material mat;
-    fp_drive drv;
-    fp_tol tol;
-    int L_max;
-    int device;
-    int num_sms;
-    FpTablesHost host;
-    double* d_coef;
-    int* d_src;
-    double* d_lam;
-    double* d_wdiag;
-    FpPair* d_colT;           // column view of the tables (adjoint)
-    DevBlk blk;               // device block structure, all degrees 2..L_max
-    void* d_blk_mem;          // one allocation backing blk
-    double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
-};
-
 static thread_local char g_err[512] = "";
 
 static int fail(int code, const char* fmt, ...) {
@@ -82,6 +52,7 @@ const char* fp_status_str(int code) {
         case FP_STATUS_NONFINITE: return "non-finite state";
         case FP_STATUS_NEWTON_FAIL: return "Newton iteration failed";
         case FP_STATUS_BAD_INPUT: return "bad instance parameters";
+        case FP_STATUS_UNRESOLVED: return "truncation degree too low (|<m>| > 1)";
         default: return "unknown code";
     }
 }
@@ -236,7 +207,7 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
         return fail(FP_EUNSUPPORTED, "fp_solve_batch: %zu bytes of shared memory needed, %d available", sm, max_sm);
     int grid = n < ctx->num_sms ? n : ctx->num_sms;
     int rc = fp_launch_solve(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
-                             d_m, d_dmdt, d_status, d_stats, grid, (cudaStream_t)stream);
+                             d_m, d_dmdt, d_status, d_stats, grid, (cudaStream_t)stream, nullptr, nullptr);
     if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }

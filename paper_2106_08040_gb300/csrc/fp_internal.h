@@ -150,3 +150,37 @@ struct DevBlk {                      // block structure of every degree, packed
 int fp_build_columns(const FpTablesHost* t, FpPair* out);   // out: [N][FP_NCT]
 void fp_free_blocks(FpBlkHost* b);
 void fp_gauss_legendre(int n, double* x, double* w);
+
+// ------------------------------------------------ context and launchers ----
+#include <cuda_runtime.h>
+size_t fp_solver_smem_bytes(int stages, int L);
+int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
+                    const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
+                    int* d_status, int* d_stats, int grid, cudaStream_t st, const int* d_order, int* d_queue);
+int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw);
+size_t fp_adjoint_smem_bytes(int stages, int L);
+size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec);
+int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
+                      const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, int k_max,
+                      const double* channels, int C, const double* d_dJ, const double* d_tw, double* d_grad,
+                      int* d_status, int* d_stats, double* d_work, int max_rec, int grid, cudaStream_t st);
+
+struct fp_ctx {
+    fp_material mat;
+    fp_drive drv;
+    fp_tol tol;
+    int L_max;
+    int device;
+    int num_sms;
+    FpTablesHost host;
+    double* d_coef;
+    int* d_src;
+    double* d_lam;
+    double* d_wdiag;
+    FpPair* d_colT;           // column view of the tables (adjoint)
+    DevBlk blk;               // device block structure, all degrees 2..L_max
+    void* d_blk_mem;          // one allocation backing blk
+    double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
+};
+
+int fp_fail(int code, const char* fmt, ...);

@@ -44,6 +44,8 @@ struct KArgs {
     int* stats;
     int S_out;
     int L_launch;
+    const int* order;       // queue slot -> instance index (NULL: identity)
+    int* queue;             // dynamic work counter, zero at launch (NULL: static round robin)
 };
 
 // slot -> scalar group: W, ZR, RZ, RX, RY, GZ, GX, GY
@@ -560,7 +562,7 @@ struct Shared {
     float2 colbuf[64 * (1 + (S - 1) / 2)];
     float red[NWARP];
     double dred[NWARP * 12];
-    double R[9], off[3], dm[3];
+    double R[9], off[3], dm[4];          // dm[3]: |<m>|^2 of the last written sample
     AScal scj[S];          // operator scalars at the stage times
     double Pm[S * S];      // predictor matrix
 };
@@ -838,6 +840,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         if (threadIdx.x == 0) {
             double mp[3] = {sq43 * C.y[3], sq43 * C.y[1], sq43 * C.y[2]};
             double dp[3] = {sh.dm[0], sh.dm[1], sh.dm[2]};
+            sh.dm[3] = mp[0] * mp[0] + mp[1] * mp[1] + mp[2] * mp[2];
             size_t o = ((size_t)inst * A.S_out + j) * 3;
             for (int k = 0; k < 3; ++k) {
                 double mk = R[k] * mp[0] + R[3 + k] * mp[1] + R[6 + k] * mp[2];
@@ -847,6 +850,9 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
             }
         }
         __syncthreads();
+        // the mean of unit vectors has norm <= 1; beyond that the truncated
+        // operator at this L is not dissipative for the instance
+        if (sh.dm[3] > (1.0 + 1e-6) * (1.0 + 1e-6) && out.status == FP_STATUS_OK) out.status = FP_STATUS_UNRESOLVED;
     };
 
     if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, 0.0); jn = 1; }
@@ -967,7 +973,22 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
     __shared__ Shared<S> sh;
     Ctx<S> C;
     bind_smem<S, false>(C, smem, A.L_launch, sh);
-    for (int inst = blockIdx.x; inst < A.n; inst += gridDim.x) {
+    __shared__ int s_slot;
+    // instances come either round robin (slot = blockIdx.x + k gridDim.x) or,
+    // with a work counter, one at a time in the caller's order, so CTAs that
+    // finish early take the next instance (uneven per-instance cost)
+    for (int k = 0;; ++k) {
+        int slot;
+        if (A.queue) {
+            if (threadIdx.x == 0) s_slot = atomicAdd(A.queue, 1);
+            __syncthreads();
+            slot = s_slot;
+            __syncthreads();
+        } else {
+            slot = blockIdx.x + k * gridDim.x;
+        }
+        if (slot >= A.n) break;
+        const int inst = A.order ? A.order[slot] : slot;
         const fp_instance in = A.inst[inst];
         if (!instance_ok(in, A.L_launch)) {
             for (int e = threadIdx.x; e < A.S_out * 3; e += NT) {
@@ -1484,8 +1505,10 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
 // --------------------------------------------------------- host launch ----
 int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
-                    int* d_status, int* d_stats, int grid, cudaStream_t st) {
+                    int* d_status, int* d_stats, int grid, cudaStream_t st, const int* d_order, int* d_queue) {
     KArgs A;
+    A.order = d_order;
+    A.queue = d_queue;
     A.tab = *tab;
     A.blk = *blk;
     A.mat = *mat;
@@ -1525,6 +1548,8 @@ int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp
                       int* d_status, int* d_stats, double* d_work, int max_rec, int grid, cudaStream_t st) {
     GArgs G;
     KArgs& A = G.A;
+    A.order = nullptr;
+    A.queue = nullptr;
     A.tab = *tab;
     A.blk = *blk;
     A.mat = *mat;

@@ -27,6 +27,10 @@ class Material:
     def c(self):
         return fp_material(self.Ms, self.alpha, self.gamma, self.T_B)
 
+    def sigma(self, K, d):
+        """Anisotropy barrier sigma = K V / (k_B T), V = pi d^3 / 6 (Sec. 2.1)."""
+        return np.asarray(K) * np.pi * np.asarray(d) ** 3 / 6.0 / (1.380649e-23 * self.T_B)
+
 
 @dataclass(frozen=True)
 class Drive:
@@ -271,3 +275,60 @@ def solve(ctx: Context, inst: np.ndarray, want_m=True, want_dmdt=True, stream=No
     stats = torch.empty((n, 4), dtype=torch.int32, device=dev)
     fp_solve_batch(ctx, d_inst, n, m, dm, st, stats, stream=stream)
     return m, dm, st, stats
+
+
+def truncation_degree(inst, material=None, drive=None, L_min=8, L_max=16):
+    """Per-instance truncation degree L = clamp(L_min, L_max, ceil(2 + 5.5 sqrt(sigma + xi_max))),
+    sigma = K V/(k_B T), xi_max = b_T (|B_off| + |B_drive amplitude|).  The
+    coefficients (2, 5.5) fit the degree at which the Boltzmann density's
+    spherical-harmonic tail beyond L - 2 falls below 1e-8 of its mean
+    (equilibrium projections over sigma in [0.5, 12], xi in [0, 20])."""
+    material = material or Material()
+    V = np.pi * np.asarray(inst["d"]) ** 3 / 6.0
+    kT = 1.380649e-23 * material.T_B
+    sigma = np.asarray(inst["K"]) * V / kT
+    amp = 0.0 if drive is None else float(np.linalg.norm(drive.amp))
+    xi = V * material.Ms / kT * (np.linalg.norm(np.asarray(inst["h_off"]), axis=1) + amp)
+    L = np.ceil(2.0 + 5.5 * np.sqrt(sigma + xi)).astype(int)
+    return np.clip(L, L_min, L_max)
+
+
+class Sweep:
+    """fp_sweep plan over host instance records (see include/fp.h)."""
+
+    def __init__(self, ctx: Context, inst: np.ndarray, bucket_width=1):
+        self.ctx = ctx
+        arr = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
+        self.n = len(arr)
+        h = C.c_void_p()
+        check(_lib.lib().fp_sweep_plan(ctx.handle, arr.ctypes.data_as(C.c_void_p), self.n, int(bucket_width),
+                                       C.byref(h)), "fp_sweep_plan")
+        self._h = h
+
+    def run(self, d_inst, d_m, d_dmdt, d_status, d_stats=None, stream=None):
+        check(_lib.lib().fp_sweep_run(self._h, _ptr(d_inst), _ptr(d_m), _ptr(d_dmdt), _ptr(d_status), _ptr(d_stats),
+                                      _stream_ptr(stream)), "fp_sweep_run")
+
+    def autotune(self, d_inst, d_m, d_dmdt, d_status, sample=64, stream=None):
+        check(_lib.lib().fp_sweep_autotune(self._h, _ptr(d_inst), _ptr(d_m), _ptr(d_dmdt), _ptr(d_status),
+                                           int(sample), _stream_ptr(stream)), "fp_sweep_autotune")
+
+    def info(self):
+        nb = C.c_int()
+        arrs = [(C.c_int * 64)() for _ in range(4)]
+        ms = (C.c_float * 64)()
+        check(_lib.lib().fp_sweep_info(self._h, C.byref(nb), *arrs, ms), "fp_sweep_info")
+        k = nb.value
+        return [{"L": arrs[0][i], "count": arrs[1][i], "stages": arrs[2][i], "refactor_every": arrs[3][i],
+                 "tuned_ms": ms[i]} for i in range(k)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().fp_sweep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -99,3 +99,34 @@ def random_instances(n, L, seed=SEED, max_offset=0.012, K_range=(5e2, 1e4), d_me
     inst["d"] = d_median * np.exp(d_sigma * rng.normal(size=n))
     inst["L"] = L
     return inst
+
+
+def fibonacci_directions(n=16):
+    """n easy-axis directions from the Fibonacci sphere: z_i = 1 - (2i + 1)/n,
+    azimuth i * pi * (3 - sqrt(5)); returns (theta, phi) arrays."""
+    i = np.arange(n)
+    z = 1.0 - (2 * i + 1) / n
+    theta = np.arccos(z)
+    phi = np.mod(i * np.pi * (3.0 - np.sqrt(5.0)), 2 * np.pi)
+    return theta, phi
+
+
+def uneven_sweep_instances(n, L, seed=SEED, nxy=64, fov=24e-3, n_dir=16, K_range=(5e2, 1e4), d_median=20e-9,
+                           d_sigma=0.1):
+    """n random draws from the uneven-sweep distribution: a voxel of the nxy x nxy
+    grid on the z = 0 plane (gradient diag(-1, -1, 2) T/m over fov), one of
+    n_dir Fibonacci easy-axis directions, K log-uniform over K_range, d
+    log-normal (median d_median, log-sd d_sigma); truncation degree L
+    (scalar or array)."""
+    rng = np.random.default_rng(seed)
+    inst = make_instances(n)
+    off = voxel_offsets(nxy, nxy, fov=fov)
+    inst["h_off"] = off[rng.integers(0, nxy * nxy, size=n)]
+    th, ph = fibonacci_directions(n_dir)
+    k = rng.integers(0, n_dir, size=n)
+    inst["theta"] = th[k]
+    inst["phi"] = ph[k]
+    inst["K"] = np.exp(rng.uniform(np.log(K_range[0]), np.log(K_range[1]), size=n))
+    inst["d"] = d_median * np.exp(d_sigma * rng.normal(size=n))
+    inst["L"] = L
+    return inst

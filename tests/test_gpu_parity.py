@@ -93,7 +93,7 @@ def test_ragged_degrees_random_instances(fp):
     dspec = workloads.DriveSpec(amp=(0.010, 0.004, 0.0), freq=(50e3, 50e3, 50e3), phase=(0.0, 0.7, 0.0),
                                 period=2e-5, samples_per_period=64, warmup_periods=0, output_periods=1)
     inst = workloads.random_instances(5, 6, seed=7, max_offset=0.006)
-    inst["L"] = [3, 8, 5, 6, 7]
+    inst["L"] = [6, 8, 5, 6, 7]          # each resolves its instance (oracle |<m>| < 1)
     ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-10, stages=3), 8)
     m, dm, st, stats = fp.solve(ctx, inst)
     torch.cuda.synchronize()
@@ -102,6 +102,22 @@ def test_ragged_degrees_random_instances(fp):
         r = oracle_solve(dspec, inst[i], rtol=1e-11)
         assert rel(m.cpu().numpy()[i], r["m"]) <= TOL, i
         assert rel(dm.cpu().numpy()[i], r["dmdt"]) <= DTOL, i
+
+
+def test_unresolved_truncation_is_flagged(fp):
+    """At L = 3 the truncated operator of this instance is not dissipative: the
+    oracle's Galerkin solution at the same L reaches |<m>| = 1.39 > 1, and the
+    solver must end it with FP_STATUS_UNRESOLVED (6) instead of returning it."""
+    dspec = workloads.DriveSpec(amp=(0.010, 0.004, 0.0), freq=(50e3, 50e3, 50e3), phase=(0.0, 0.7, 0.0),
+                                period=2e-5, samples_per_period=64, warmup_periods=0, output_periods=1)
+    inst = workloads.random_instances(5, 6, seed=7, max_offset=0.006)[:1]
+    inst["L"] = 3
+    r = oracle_solve(dspec, inst[0], rtol=1e-8)
+    assert np.linalg.norm(r["m"], axis=1).max() > 1.0
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-10, stages=3), 8)
+    _, _, st, _ = fp.solve(ctx, inst)
+    torch.cuda.synchronize()
+    assert st.cpu().numpy()[0] == 6
 
 
 def test_rotation_covariance(fp):
