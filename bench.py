@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--instances", type=int, default=0, help="profiling: first N voxels only (0 = all)")
     p.add_argument("--warmup-periods", type=int, default=1, help="profiling: warm-up periods per instance")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    p.add_argument("--no-sweep", action="store_true", help="skip the uneven-sweep measurement")
+    p.add_argument("--sweep-instances", type=int, default=2048)
     return p.parse_args()
 
 
@@ -69,6 +72,19 @@ def workload_for_rank(rank, args):
         d["warmup_periods"] = args.warmup_periods
         dspec = workloads.DriveSpec(**d)
     return dspec, inst
+
+
+def max_over_ranks(x, dist, device):
+    """Max of a per-rank scalar over the process group (the slowest rank's time)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_per_rank, periods, ms):
+    """Whole-job instance-periods/s: every rank solves its own n instances."""
+    return world * n_per_rank * periods / (ms * 1e-3)
 
 
 # ----------------------------------------------------------------- clocks ----
@@ -209,6 +225,137 @@ def cpu_oracle_sample(dspec, inst, target_s, rtol=1e-10):
                       % (cores, ns, ip, wall)}
 
 
+# --------------------------------------------------------------- surrogate --
+SUR_FLOPS_PER_QUERY = 2.0 * (7 * 512 + 3 * 512 * 512 + 512 * 800)   # algorithmic (unpadded input)
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured (MEASURED_PEAKS.json %s)" % key
+    except Exception:
+        return fallback, "fallback"
+
+
+def surrogate_leg(fp, dev):
+    """Trained surrogate ensemble: inference throughput on the 40^3 x 16
+    (1,024,000-query) grid, and its error and speed against the FP solve on
+    fresh draws from its training domain."""
+    import torch
+    from paper_2106_08040_gb300 import surrogate, surrogate_train as stt, workloads
+    path = stt.DEFAULT_OUT
+    base, ext = os.path.splitext(path)
+    if not os.path.exists("%s.m0%s" % (base, ext)):
+        return {"unavailable": "no trained weights at %s" % os.path.relpath(path, ROOT)}
+    ens = stt.Ensemble.load(path, device=dev)
+    # query grid: 40^3 offsets over a 24 mm cube (gradient diag(-1, -1, 2) T/m) x 16 Fibonacci axes
+    g = -12e-3 + (np.arange(40) + 0.5) * 24e-3 / 40
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    off = np.stack([-X.ravel(), -Y.ravel(), 2 * Z.ravel()], 1)
+    th, ph = workloads.fibonacci_directions(16)
+    q = off.shape[0] * 16
+    rng = np.random.default_rng(5)
+    xq = np.empty((q, 7), dtype=np.float32)
+    xq[:, 0:3] = np.repeat(off, 16, axis=0)
+    xq[:, 3] = np.tile(th, off.shape[0])
+    xq[:, 4] = np.tile(ph, off.shape[0])
+    xq[:, 5] = rng.uniform(np.log(5e2), np.log(1e4), size=q)            # ln K, K log-uniform
+    xq[:, 6] = np.log(20e-9) + 0.1 * rng.normal(size=q)                 # ln d, d log-normal
+    x = torch.from_numpy(xq).to(dev)
+    for _ in range(3):
+        ens.infer(x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        ens.infer(x)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    q_per_s = q / (ms * 1e-3)
+    # judge: fresh draws from the training domain, solved by the FP path
+    draw = workloads.uneven_sweep_instances(1024, 16, seed=7)
+    draw = draw[fp.Material().sigma(draw["K"], draw["d"]) <= 12.0][:152]
+    ctx = stt.solver_context(16, 1e-7)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    y, st = stt.solve_signals(ctx, draw)
+    t_solve = time.time() - t0
+    ctx.close()
+    ok = st == 0
+    mean, spread = ens.infer(torch.from_numpy(surrogate.features(draw).astype(np.float32)).to(dev))
+    err = stt.relative_errors(mean.cpu().numpy().astype(np.float64)[ok], y[ok])
+    spr = spread.cpu().numpy()[ok]
+    solver_per_s = len(draw) / t_solve
+    peak, src = measured_peak("bf16_tflops", 1900.0)
+    achieved = 2 * SUR_FLOPS_PER_QUERY * q / (ms * 1e-3) / 1e12
+    gate = {}
+    for g_thr in (1e-3, 1e-2, 3e-2, 1e-1):
+        acc = spr <= g_thr
+        f_rej = 1.0 - acc.mean()
+        t_per_q = 1.0 / q_per_s + f_rej / solver_per_s
+        gate["%g" % g_thr] = {"accepted": float(acc.mean()),
+                              "err_p90_accepted": float(np.quantile(err[acc], 0.9)) if acc.any() else None,
+                              "speedup_with_fallback": float((1.0 / solver_per_s) / t_per_q)}
+    return {"queries": q, "ms": ms, "queries_per_s": q_per_s, "ensemble": 2,
+            "solver_instances_per_s": solver_per_s, "speedup_vs_solver": q_per_s / solver_per_s,
+            "holdout": int(ok.sum()), "rel_err_median": float(np.median(err)),
+            "rel_err_p90": float(np.quantile(err, 0.9)), "gate_on_member_spread": gate,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": src,
+                         "kernel": "mlp_gemm_kernel (tcgen05 BF16, 2 members x 5 layers)"},
+            "judge": "fp_solve_batch + fp_signal, L = 16, rtol 1e-7, 152 fresh draws of the training domain"}
+
+
+def sweep_leg(fp, dev, n_inst):
+    """Uneven sweep: draws of the uneven-sweep distribution (64 x 64 voxel
+    offsets, 16 Fibonacci axes, K log-uniform, d log-normal) with L per
+    instance from the truncation rule (8..16), planned, autotuned and run as
+    one graph; instance-periods/s."""
+    import torch
+    from paper_2106_08040_gb300 import workloads
+    dspec = workloads.drive_lissajous()
+    drv = fp.Drive(**dspec.__dict__)
+    draw = workloads.uneven_sweep_instances(2 * n_inst, 16, seed=11)
+    draw = draw[fp.Material().sigma(draw["K"], draw["d"]) <= 12.0][:n_inst]
+    draw["L"] = fp.truncation_degree(draw, drive=drv, L_min=8, L_max=16)
+    ctx = fp.Context(fp.Material(), drv, fp.Tol(rtol=1e-9, stages=3), 16)
+    n = len(draw)
+    S = ctx.num_samples()
+    d_inst = fp.instances_to_device(draw, dev)
+    m = torch.empty((n, S, 3), dtype=torch.float64, device=dev)
+    dm = torch.empty_like(m)
+    st = torch.empty((n,), dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    sw = fp.Sweep(ctx, draw, bucket_width=2)
+    t0 = time.time()
+    with torch.cuda.stream(s):
+        sw.autotune(d_inst, m, dm, st, sample=32, stream=s)
+    s.synchronize()
+    t_tune = time.time() - t0
+    with torch.cuda.stream(s):
+        sw.run(d_inst, m, dm, st, stream=s)            # capture
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        sw.run(d_inst, m, dm, st, stream=s)            # graph replay
+        e1.record(s)
+    s.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = st.cpu().numpy()
+    periods = dspec.warmup_periods + dspec.output_periods
+    out = {"instances": n, "L_hist": {int(k): int(v) for k, v in zip(*np.unique(draw["L"], return_counts=True))},
+           "ms": ms, "instance_periods_per_s": n * periods / (ms * 1e-3), "status_ok": int((status == 0).sum()),
+           "autotune_s": t_tune, "buckets": sw.info(),
+           "workload": "uneven sweep draws (sigma <= 12), L by truncation rule in [8, 16], Lissajous drive, "
+                       "1 warm-up + 1 output period, rtol 1e-9"}
+    sw.close()
+    ctx.close()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm --
 def run_gpu(args):
     import torch
@@ -274,13 +421,11 @@ def run_gpu(args):
     ms = sum(step_ms) / args.steps
     t_solve = sum(solve_ms) / args.steps
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(ms, dist, dev)
     status = st.cpu().numpy()
     sts = stats.cpu().numpy()
     periods = drv.warmup_periods + drv.output_periods
-    value = world * n * periods / (ms * 1e-3)
+    value = job_throughput(world, n, periods, ms)
     # roofline of the dominant kernel (the solver): FP64 pipe
     flops = float(fp64_flops_per_instance(sts, (L + 1) ** 2, nnz, args.stages).sum())
     achieved = flops / (t_solve * 1e-3) / 1e12
@@ -306,9 +451,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     out = None
     if rank == 0:
         out = {
@@ -323,7 +466,7 @@ def run_gpu(args):
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": "independent instances; weak scaling, rank r uses easy-axis angle 15 deg*r"},
             "gpu_launches": 2 * args.steps,
-            "e2e": {"value": (world * n * periods / (e2e_ms * 1e-3)) if e2e_ms == e2e_ms else None, "unit": UNIT,
+            "e2e": {"value": job_throughput(world, n, periods, e2e_ms) if e2e_ms == e2e_ms else None, "unit": UNIT,
                     "h2d_bytes_per_step": int(h_inst.numel()), "d2h_bytes_per_step": int(h_ph.numel() * 8)},
             "roofline": roof,
             "clocks": clk,
@@ -334,6 +477,11 @@ def run_gpu(args):
                                 "fp64_flops_per_step": flops},
         }
     ctx.close()
+    if rank == 0 and world == 1:
+        if not args.no_surrogate:
+            out["surrogate"] = surrogate_leg(fp, dev)
+        if not args.no_sweep:
+            out["sweep"] = sweep_leg(fp, dev, args.sweep_instances)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -9,12 +9,12 @@
 // beside W, so one kernel shape serves forward, dX and dW.
 //
 // Tile: 128 rows (UMMA M = 128, one CTA), BN columns (64..256), K blocks of
-// 64 bf16 = one 128-byte swizzle row; STAGES-deep TMA ring.  Warp 0 lane 0
-// issues TMA, warp 1 lane 0 issues tcgen05.mma, warp 2 owns the TMEM
-// allocation, and all four warps run the epilogue (warp w reads TMEM lanes
-// 32w..32w+31, i.e. tile rows 32w..32w+31).  Every wait is bounded in time; a
-// wait that gives up sets *err and the CTA drains and frees TMEM before it
-// returns.
+// 64 bf16 = one 128-byte swizzle row; STAGES-deep TMA ring sized for two CTAs
+// per SM.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma, warp 2
+// owns the TMEM allocation, and all eight warps run the epilogue (warp w reads
+// TMEM lanes 32 (w % 4) .. + 31, i.e. those tile rows, and half of the
+// columns).  Every wait is bounded in time; a wait that gives up sets *err and
+// the CTA drains and frees TMEM before it returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -29,7 +29,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int NTHREADS = 128;
+constexpr int NTHREADS = 256;                 // 8 warps: all run the epilogue
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
 enum Epi : int {
@@ -164,7 +164,9 @@ template <int BN> struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (200 * 1024) / STAGE > 8 ? 8 : (200 * 1024) / STAGE;
+    // ring depth sized so that two CTAs fit on one SM (about 113 KB each):
+    // one CTA's epilogue then overlaps the other's TMA/MMA main loop
+    static constexpr int STAGES = (110 * 1024) / STAGE > 6 ? 6 : (110 * 1024) / STAGE;
     static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr int SMEM = STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms need 1024-byte tiles");
@@ -247,7 +249,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int 
 
 // ------------------------------------------------------------------ kernel ----
 template <int BN, int EPI>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, 2)
 mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, EpiParams P) {
     using C = Cfg<BN>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -258,7 +260,8 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     int* abort_flag = (int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // N tiles of one row block are adjacent CTAs, so the A tile is re-read from L2
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = P.nk;
 
     if (threadIdx.x == 0) {
@@ -334,10 +337,13 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (!acc_ok) {
         if (lane == 0) atomicOr(P.err, 4);
     } else if (!*(volatile int*)abort_flag && nk > 0) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+        // warp w may read TMEM lanes 32 (w % 4) .. + 31; warps w and w + 4 split the columns
+        const int lg = warp & 3, half = warp >> 2;
+        const int row = m0 + lg * 32 + lane;
+        const uint32_t tw = tmem + ((uint32_t)(lg * 32) << 16);
+        constexpr int CH = ((BN / 16) + 1) / 2 * 16;       // columns of the first half, multiple of 16
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
+        for (int c = half * CH; c < (half ? BN : CH); c += 16) {
             float v[16];
             tmem_ld16(tw + c, v);
             if (n0 + c < P.N) epilogue_chunk<EPI>(P, row, n0 + c, v);
@@ -391,7 +397,7 @@ int launch_t(const CUtensorMap& a, const CUtensorMap& b, const EpiParams& P, int
     if (cudaFuncSetAttribute(mlp_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
         cudaSuccess)
         return FP_ECUDA;
-    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     mlp_gemm_kernel<BN, EPI><<<grid, NTHREADS, C::SMEM, st>>>(a, b, P);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
 }

@@ -110,18 +110,26 @@ class Surrogate:
         check(_lib.lib().fp_surrogate_adam(C.byref(self.train_state), None, None, 0.0, 0.9, 0.999, 1e-8, 0,
                                            _stream(stream)), "fp_surrogate_adam")
 
-    def set_normalisation(self, x, y):
-        """Input shift/scale and output shift/scale from training data (host arrays)."""
+    def set_normalisation(self, x, y, per_output=False):
+        """Input shift/scale and output shift/scale from training data (host
+        arrays).  By default the outputs share one scale (the RMS deviation of
+        all of them), so the squared-error loss weighs each harmonic as the
+        relative L2 signal error does; per_output=True standardises each
+        output column instead."""
         import torch
         x = np.asarray(x, dtype=np.float64)
         y = np.asarray(y, dtype=np.float64)
         xs = x.std(axis=0)
-        ys = y.std(axis=0)
         self.in_shift.copy_(torch.from_numpy(x.mean(axis=0).astype(np.float32)))
         self.in_scale.copy_(torch.from_numpy((1.0 / np.where(xs > 0, xs, 1.0)).astype(np.float32)))
-        self.out_shift.copy_(torch.from_numpy(y.mean(axis=0).astype(np.float32)))
-        floor = 1e-3 * max(float(ys.max()), 1e-30)
-        self.out_scale.copy_(torch.from_numpy(np.maximum(ys, floor).astype(np.float32)))
+        mu = y.mean(axis=0)
+        self.out_shift.copy_(torch.from_numpy(mu.astype(np.float32)))
+        if per_output:
+            ys = y.std(axis=0)
+            ys = np.maximum(ys, 1e-3 * max(float(ys.max()), 1e-30))
+        else:
+            ys = np.full(y.shape[1], max(float(np.sqrt(np.mean((y - mu) ** 2))), 1e-30))
+        self.out_scale.copy_(torch.from_numpy(ys.astype(np.float32)))
 
     def workspace(self, q, training):
         import torch
@@ -189,8 +197,9 @@ class Surrogate:
                 "out_shift": self.out_shift.cpu().numpy(), "out_scale": self.out_scale.cpu().numpy()}
 
     def save(self, path, **meta):
+        """Weights as their BF16 bit patterns (what inference uses), the rest in FP32."""
         s = self.state()
-        arrs = {"W%d" % l: s["Wm"][l] for l in range(LAYERS)}
+        arrs = {"W%d" % l: self.W[l].cpu().view(__import__("torch").int16).numpy() for l in range(LAYERS)}
         arrs.update({"b%d" % l: s["bm"][l] for l in range(LAYERS)})
         arrs.update({k: s[k] for k in ("in_shift", "in_scale", "out_shift", "out_scale")})
         arrs.update({"meta_" + k: np.asarray(v) for k, v in meta.items()})
@@ -202,7 +211,12 @@ class Surrogate:
         z = np.load(path)
         s = cls(device=device)
         for l in range(LAYERS):
-            s.Wm[l].copy_(torch.from_numpy(z["W%d" % l]))
+            w = z["W%d" % l]
+            if w.dtype == np.int16:
+                w = torch.from_numpy(w).view(torch.bfloat16).float()
+            else:
+                w = torch.from_numpy(w)
+            s.Wm[l].copy_(w)
             s.bm[l].copy_(torch.from_numpy(z["b%d" % l]))
         for k in ("in_shift", "in_scale", "out_shift", "out_scale"):
             getattr(s, k).copy_(torch.from_numpy(z[k]))
