@@ -1,0 +1,81 @@
+"""Adjoint-driven parameter fits on synthetic measurements.
+
+The measurement over a voxel grid is a weighted superposition of the signals
+of a few hidden parameter sets (K, d, theta, phi) plus Gaussian noise; a
+candidate parameter set p explains it with the single-set model phi_hat(v; p)
+at every voxel v (the superposition and single-function-vector models of
+Sec. 2.2, M1, with the transfer function left out, R7).  The misfit
+
+    J(p) = sum_v sum_{c, k} |phi_hat_{c,k}(v; p) - u_{c,k}(v)|^2
+
+and its gradient dJ/d(K, d, theta, phi) come from one forward solve per voxel
+(fp_solve_batch + fp_signal) and one adjoint per voxel (fp_grad with
+dJ/dphi_hat = 2 (phi_hat - u)), summed over the voxels of each candidate.
+"""
+import numpy as np
+
+from . import fp, workloads
+
+
+class FitProblem:
+    def __init__(self, dspec, offsets, L, k_max, rtol=1e-9, channels=((1.0, 0.0, 0.0), (0.0, 1.0, 0.0))):
+        self.dspec, self.offsets, self.L, self.k_max = dspec, np.asarray(offsets), L, k_max
+        self.ch = np.asarray(channels, dtype=np.float64)
+        self.ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=rtol, stages=3), L)
+
+    def instances(self, params):
+        """One instance per (candidate, voxel): params [P, 4] = (K, d, theta, phi)."""
+        params = np.atleast_2d(params)
+        nv = len(self.offsets)
+        inst = workloads.make_instances(len(params) * nv)
+        inst["h_off"] = np.tile(self.offsets, (len(params), 1))
+        for j, key in enumerate(("K", "d", "theta", "phi")):
+            inst[key] = np.repeat(params[:, j], nv)
+        inst["L"] = self.L
+        return inst
+
+    def signals(self, params):
+        """phi_hat [P, V, C, k_max + 1, 2] (device tensor) and status [P * V]."""
+        import torch
+        inst = self.instances(params)
+        _, dm, st, _ = fp.solve(self.ctx, inst, want_m=False)
+        ph = torch.empty((len(inst), len(self.ch), self.k_max + 1, 2), dtype=torch.float64, device=dm.device)
+        fp.fp_signal(self.ctx, dm, len(inst), self.k_max, self.ch, ph)
+        P = np.atleast_2d(params).shape[0]
+        return ph.view(P, len(self.offsets), len(self.ch), self.k_max + 1, 2), st
+
+    def measurement(self, hidden, weights, noise=0.01, seed=workloads.SEED):
+        """sum_i w_i phi_hat(v; p_i) + Gaussian noise of `noise` x the RMS signal."""
+        ph, st = self.signals(hidden)
+        if not bool((st == 0).all()):
+            raise RuntimeError("hidden parameter sets did not solve: %s" % st.cpu().numpy())
+        import torch
+        w = torch.as_tensor(np.asarray(weights, dtype=np.float64), device=ph.device).view(-1, 1, 1, 1, 1)
+        u = (w * ph).sum(dim=0)
+        rms = float(u.pow(2).mean().sqrt())
+        g = torch.Generator(device=ph.device)
+        g.manual_seed(int(seed))
+        return u + noise * rms * torch.randn(u.shape, generator=g, device=u.device, dtype=u.dtype)
+
+    def misfit_and_grad(self, params, u):
+        """J [P] and dJ/d(K, d, theta, phi) [P, 4] for candidate sets params [P, 4]."""
+        import torch
+        params = np.atleast_2d(params)
+        inst = self.instances(params)
+        ph, st = self.signals(params)
+        r = ph - u.unsqueeze(0)
+        J = r.pow(2).sum(dim=(1, 2, 3, 4))
+        n = len(inst)
+        dev = ph.device
+        d_inst = fp.instances_to_device(inst, dev)
+        dJ = (2.0 * r).reshape(n, len(self.ch), self.k_max + 1, 2).contiguous()
+        grad = torch.empty((n, 4), dtype=torch.float64, device=dev)
+        gst = torch.empty((n,), dtype=torch.int32, device=dev)
+        work = torch.empty(fp.fp_grad_workspace_bytes(self.ctx, n), dtype=torch.uint8, device=dev)
+        fp.fp_grad(self.ctx, d_inst, n, self.k_max, self.ch, dJ, grad, gst, work)
+        ok = bool((st == 0).all()) and bool((gst == 0).all())
+        g = grad.view(len(params), len(self.offsets), 4).sum(dim=1)
+        return J.cpu().numpy(), g.cpu().numpy(), ok
+
+    def close(self):
+        self.ctx.close()
