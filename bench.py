@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FP instance-periods/s at ≤1e-9 rel err vs FP64 oracle; surrogate speedup at 1e-3"
 UNIT = "instance-periods/s"
 L2_FLUSH_BYTES = 256 << 20
+SOLVER_S5_TRAFFIC_BYTES = (2.43 + 95.76) * 1e6      # dram read + write of one fp_solve_kernel<5> launch
 
 
 def parse():
@@ -41,7 +42,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--stages", type=int, default=3)
+    p.add_argument("--stages", type=int, default=5, help="Radau IIA stages: 5 (order 9) or 3 (order 5)")
     p.add_argument("--rtol", type=float, default=1e-9)
     p.add_argument("--cpu-sample-s", type=float, default=20.0, help="target CPU seconds per oracle process")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -50,6 +51,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the uneven-sweep measurement")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     p.add_argument("--sweep-instances", type=int, default=2048)
     return p.parse_args()
 
@@ -308,6 +310,44 @@ def surrogate_leg(fp, dev):
             "judge": "fp_solve_batch + fp_signal, L = 16, rtol 1e-7, 152 fresh draws of the training domain"}
 
 
+def adjoint_leg(fp, dev, n_inst=152):
+    """Discrete adjoint (fp_grad) on the first voxels of the system-matrix batch:
+    gradients dJ/d(K, d, theta, phi) of a seeded linear functional of phi_hat,
+    timed against the forward solve + phi_hat of the same instances."""
+    import torch
+    from paper_2106_08040_gb300 import workloads
+    dspec, inst = workloads.system_matrix_workload()
+    inst = inst[:n_inst]
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=3), 16)
+    n, K = len(inst), 816
+    ch = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    d_inst = fp.instances_to_device(inst, dev)
+    dJ = torch.from_numpy(np.random.default_rng(3).normal(size=(n, 2, K + 1, 2))).to(dev)
+    grad = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    st = torch.empty((n,), dtype=torch.int32, device=dev)
+    work = torch.empty(fp.fp_grad_workspace_bytes(ctx, n), dtype=torch.uint8, device=dev)
+    S = ctx.num_samples()
+    dm = torch.empty((n, S, 3), dtype=torch.float64, device=dev)
+    ph = torch.empty((n, 2, K + 1, 2), dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    fp.fp_solve_batch(ctx, d_inst, n, None, dm, st, None)
+    fp.fp_signal(ctx, dm, n, K, ch, ph)
+    ev[1].record()
+    fp.fp_grad(ctx, d_inst, n, K, ch, dJ, grad, st, work)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_f, t_a = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    periods = dspec.warmup_periods + dspec.output_periods
+    out = {"instances": n, "forward_ms": t_f, "adjoint_ms": t_a, "adjoint_over_forward": t_a / t_f,
+           "gradients_per_s": n / (t_a * 1e-3), "instance_periods_per_s": n * periods / (t_a * 1e-3),
+           "status_ok": int((st.cpu().numpy() == 0).sum()), "workspace_bytes": int(work.numel()),
+           "workload": "first %d voxels of the 32x32 system-matrix batch, L = 16, Radau s = 3, rtol 1e-9, "
+                       "checkpoints every 64 steps" % n}
+    ctx.close()
+    return out
+
+
 def sweep_leg(fp, dev, n_inst):
     """Uneven sweep: draws of the uneven-sweep distribution (64 x 64 voxel
     offsets, 16 Fibonacci axes, K log-uniform, d log-normal) with L per
@@ -429,8 +469,13 @@ def run_gpu(args):
     # roofline of the dominant kernel (the solver): FP64 pipe
     flops = float(fp64_flops_per_instance(sts, (L + 1) ** 2, nnz, args.stages).sum())
     achieved = flops / (t_solve * 1e-3) / 1e12
+    # DRAM bytes per launch from the one-pass ncu capture of this kernel on this workload
+    # (profiles/solver_s5_system_matrix_L16.md); null for any other configuration
+    full = n == 1024 and periods == 2 and L == 16
+    traffic = SOLVER_S5_TRAFFIC_BYTES if (full and args.stages == 5 and args.rtol == 1e-9) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak / 1e3, "unit": "TFLOP/s",
-            "frac": achieved / (peak / 1e3), "traffic": None,
+            "frac": achieved / (peak / 1e3), "traffic": traffic,
+            "traffic_source": "profiles/solver_s5_system_matrix_L16.md" if traffic else None,
             "kernel": "fp_solve_kernel<%d> (FP64 pipe)" % args.stages,
             "peak_source": "measured FP64 FMA throughput (fp_peak_fp64, this GPU, this run)"}
     # end-to-end through the public API: host instances -> solve -> phi_hat -> host
@@ -482,6 +527,8 @@ def run_gpu(args):
             out["surrogate"] = surrogate_leg(fp, dev)
         if not args.no_sweep:
             out["sweep"] = sweep_leg(fp, dev, args.sweep_instances)
+        if not args.no_adjoint:
+            out["adjoint"] = adjoint_leg(fp, dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

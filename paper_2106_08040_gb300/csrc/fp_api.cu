@@ -205,9 +205,8 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     if ((int)sm > max_sm)
         return fail(FP_EUNSUPPORTED, "fp_solve_batch: %zu bytes of shared memory needed, %d available", sm, max_sm);
-    int grid = n < ctx->num_sms ? n : ctx->num_sms;
     int rc = fp_launch_solve(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
-                             d_m, d_dmdt, d_status, d_stats, grid, (cudaStream_t)stream, nullptr, nullptr);
+                             d_m, d_dmdt, d_status, d_stats, ctx->num_sms, (cudaStream_t)stream, nullptr, nullptr);
     if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }

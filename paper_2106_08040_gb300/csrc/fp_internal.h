@@ -156,7 +156,7 @@ void fp_gauss_legendre(int n, double* x, double* w);
 size_t fp_solver_smem_bytes(int stages, int L);
 int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
-                    int* d_status, int* d_stats, int grid, cudaStream_t st, const int* d_order, int* d_queue);
+                    int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue);
 int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw);
 size_t fp_adjoint_smem_bytes(int stages, int L);
 size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec);

@@ -1505,7 +1505,7 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
 // --------------------------------------------------------- host launch ----
 int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
-                    int* d_status, int* d_stats, int grid, cudaStream_t st, const int* d_order, int* d_queue) {
+                    int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue) {
     KArgs A;
     A.order = d_order;
     A.queue = d_queue;
@@ -1522,17 +1522,29 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
     A.stats = d_stats;
     A.S_out = drv->output_periods * drv->samples_per_period;
     A.L_launch = L_launch;
-    size_t sm = fp_solver_smem_bytes(stages, L_launch);
     cudaError_t e;
     if (stages == 5) {
+        const size_t sm = fp_solver_smem_bytes(5, L_launch);
         e = cudaFuncSetAttribute(fp_solve_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return FP_ECUDA;
+        const int grid = n < num_sms ? n : num_sms;
         fp_solve_kernel<5><<<grid, NT, sm, st>>>(A);
-    } else {
-        e = cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return FP_ECUDA;
-        fp_solve_kernel<3><<<grid, NT, sm, st>>>(A);
+        return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
     }
+    // stages 3: as many CTAs per SM as registers and shared memory allow
+    // (one with the register budget of this build)
+    const size_t sm = make_layout<3>(L_launch).total;
+    int per_sm = 0;
+    cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return FP_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_solve_kernel<3>, NT, sm) != cudaSuccess) per_sm = 1;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    const int cap = per_sm * num_sms;
+    const int grid = n < cap ? n : cap;
+    fp_solve_kernel<3><<<grid, NT, sm, st>>>(A);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
 }
 

@@ -69,9 +69,8 @@ int launch_bucket(fp_sweep* sw, int bi, const fp_instance* d_inst, double* d_m, 
     int max_sm = 0;
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if ((int)sm > max_sm) return fp_fail(FP_EUNSUPPORTED, "fp_sweep: %zu bytes of shared memory at L=%d", sm, bk.L);
-    const int grid = count < c->num_sms ? count : c->num_sms;
     int rc = fp_launch_solve(bk.stages, &tab, &c->blk, &c->mat, &c->drv, &tol, d_inst, count, bk.L, d_m, d_dmdt,
-                             d_status, d_stats, grid, st, order, queue);
+                             d_status, d_stats, c->num_sms, st, order, queue);
     if (rc != FP_OK) return fp_fail(rc, "fp_sweep: launch at L=%d failed: %s", bk.L, cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }

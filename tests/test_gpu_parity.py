@@ -60,13 +60,15 @@ def test_single_instance_trace(fp, stages):
     assert rel(dm.cpu().numpy()[0], ref["dmdt"]) <= DTOL
 
 
-def test_system_matrix_full_launch_sampled_voxels(fp):
-    """Full 32 x 32 batch in one launch (as the benchmark runs it); sampled
-    voxels checked against oracle traces, every status OK."""
+@pytest.mark.parametrize("stages", [3, 5])
+def test_system_matrix_full_launch_sampled_voxels(fp, stages):
+    """Full 32 x 32 batch in one launch (as the benchmark runs it, either
+    Radau stage count); sampled voxels checked against oracle traces, every
+    status OK."""
     files = sorted(glob.glob(os.path.join(GOLD, "sysmat_L16_v*.npz")))
     assert files, "no golden voxel traces"
     dspec, inst = workloads.system_matrix_workload()
-    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=3), 16)
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=stages), 16)
     m, dm, st, stats = fp.solve(ctx, inst)
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == 0).all()
