@@ -174,8 +174,10 @@ template <int BN> struct Cfg {
 };
 
 // ---------------------------------------------------------------- epilogue ----
+// sb, ssc, ssh: bias, output scale and shift of this chunk's 16 columns (shared memory)
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int col0, float* v) {
+__device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int col0, float* v, const float* sb,
+                                               const float* ssc, const float* ssh) {
     const bool rv = row < P.M;
     if (EPI == EPI_DW) {
         if (!rv) return;
@@ -193,7 +195,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int 
         float* o = P.outf + (size_t)row * P.ldf;
         for (int i = 0; i < 16; ++i) {
             const int c = col0 + i;
-            if (c < P.N) o[c] = (v[i] + __ldg(P.bias + c)) * __ldg(P.oscale + c) + __ldg(P.oshift + c);
+            if (c < P.N) o[c] = (v[i] + sb[i]) * ssc[i] + ssh[i];
         }
         return;
     }
@@ -205,13 +207,13 @@ __device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int 
         const bool cv = c < P.N;
         float r = 0.f;
         if (EPI == EPI_HIDDEN_INFER || EPI == EPI_HIDDEN_TRAIN) {
-            const float z = v[i] + (cv ? __ldg(P.bias + c) : 0.f);
+            const float z = v[i] + sb[i];
             if (EPI == EPI_HIDDEN_TRAIN && rv && cv) P.outf[(size_t)row * P.ldf + c] = z;
             r = gelu(z);
         } else if (EPI == EPI_OUT_TRAIN) {
             if (rv && cv) {
-                const float z = v[i] + __ldg(P.bias + c);
-                const float t = (__ldg(P.y + (size_t)row * P.ldy + c) - __ldg(P.oshift + c)) / __ldg(P.oscale + c);
+                const float z = v[i] + sb[i];
+                const float t = (__ldg(P.y + (size_t)row * P.ldy + c) - ssh[i]) / ssc[i];
                 const float d = z - t;
                 lsum += d * d;
                 r = P.gscale * d;
@@ -263,6 +265,15 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // N tiles of one row block are adjacent CTAs, so the A tile is re-read from L2
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = P.nk;
+    // per-column epilogue constants of this tile, staged once (zero beyond N)
+    __shared__ float s_bias[BN], s_osc[BN], s_osh[BN];
+    for (int j = threadIdx.x; j < BN; j += NTHREADS) {
+        const int c = n0 + j;
+        const bool in = c < P.N;
+        s_bias[j] = (in && P.bias) ? P.bias[c] : 0.f;
+        s_osc[j] = (in && P.oscale) ? P.oscale[c] : 1.f;
+        s_osh[j] = (in && P.oshift) ? P.oshift[c] : 0.f;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2 * C::STAGES + 1; ++s) mbar_init(smem_u32(bars + s), 1);
@@ -346,7 +357,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         for (int c = half * CH; c < (half ? BN : CH); c += 16) {
             float v[16];
             tmem_ld16(tw + c, v);
-            if (n0 + c < P.N) epilogue_chunk<EPI>(P, row, n0 + c, v);
+            if (n0 + c < P.N) epilogue_chunk<EPI>(P, row, n0 + c, v, s_bias + c, s_osc + c, s_osh + c);
         }
     }
     tc_fence_before();
