@@ -8,13 +8,14 @@
 // epilogues, which also store transposed copies (X^T, G^T) and by keeping W^T
 // beside W, so one kernel shape serves forward, dX and dW.
 //
-// Tile: 128 rows (UMMA M = 128, one CTA), BN columns (64..256), K blocks of
-// 64 bf16 = one 128-byte swizzle row; STAGES-deep TMA ring sized for two CTAs
-// per SM.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma, warp 2
-// owns the TMEM allocation, and all eight warps run the epilogue (warp w reads
-// TMEM lanes 32 (w % 4) .. + 31, i.e. those tile rows, and half of the
-// columns).  Every wait is bounded in time; a wait that gives up sets *err and
-// the CTA drains and frees TMEM before it returns.
+// Tile: 128 rows (UMMA M = 128), BN columns (64..256), K blocks of 64 bf16 =
+// one 128-byte swizzle row; one persistent CTA per SM walks its tiles through
+// an STAGES-deep TMA ring.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues
+// tcgen05.mma into one of two TMEM accumulators (warp 1 owns the allocation),
+// and the epilogue warps 2.. drain the other accumulator (warp w reads TMEM
+// lanes 32 (w % 4) .. + 31, i.e. those tile rows, and one group of columns).
+// Every wait is bounded in time; a wait that gives up sets *err and the CTA
+// drains its copies and MMAs and frees TMEM before it returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -29,7 +30,8 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int NTHREADS = 256;                 // 8 warps: all run the epilogue
+constexpr int EPI_GROUPS = 2;                 // column groups of the epilogue, 4 warps each
+constexpr int NTHREADS = 64 + 128 * EPI_GROUPS;   // TMA warp, MMA warp, epilogue warps
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
 enum Epi : int {
@@ -164,14 +166,16 @@ template <int BN> struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    // ring depth sized so that two CTAs fit on one SM (about 113 KB each):
-    // one CTA's epilogue then overlaps the other's TMA/MMA main loop
-    static constexpr int STAGES = (110 * 1024) / STAGE > 6 ? 6 : (110 * 1024) / STAGE;
-    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    // one persistent CTA per SM: the ring takes most of the shared memory
+    static constexpr int STAGES = (196 * 1024) / STAGE > 8 ? 8 : (196 * 1024) / STAGE;
+    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;   // one accumulator
     static constexpr int SMEM = STAGES * STAGE + 1024 /* align */ + 256 /* barriers */;
     static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms need 1024-byte tiles");
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
 };
+
+constexpr int EPI_WARPS = 4 * EPI_GROUPS;    // warps 2 ..
+constexpr int MAX_EPI_COLS = 1024;           // bias / output scale staged in shared memory
 
 // ---------------------------------------------------------------- epilogue ----
 // sb, ssc, ssh: bias, output scale and shift of this chunk's 16 columns (shared memory)
@@ -192,10 +196,15 @@ __device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int 
     }
     if (EPI == EPI_OUT_INFER) {
         if (!rv) return;
-        float* o = P.outf + (size_t)row * P.ldf;
-        for (int i = 0; i < 16; ++i) {
-            const int c = col0 + i;
-            if (c < P.N) o[c] = (v[i] + sb[i]) * ssc[i] + ssh[i];
+        float* o = P.outf + (size_t)row * P.ldf + col0;
+        float r[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) r[i] = (v[i] + sb[i]) * ssc[i] + ssh[i];
+        if (col0 + 16 <= P.N && ((P.ldf & 3) == 0)) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) *(float4*)(o + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+        } else {
+            for (int i = 0; i < 16 && col0 + i < P.N; ++i) o[i] = r[i];
         }
         return;
     }
@@ -250,40 +259,49 @@ __device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int 
 }
 
 // ------------------------------------------------------------------ kernel ----
+// Persistent: one CTA per SM walks the output tiles (tile t -> row block
+// t / ntn, column block t % ntn, so neighbouring tiles share their A rows).
+// Warp 0 lane 0 streams K blocks of every tile through the TMA ring, warp 1
+// lane 0 issues the MMAs into one of two TMEM accumulators, and the epilogue
+// warps drain the other accumulator, so the epilogue of tile u overlaps the
+// main loop of tile u + 1.
 template <int BN, int EPI>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, 1)
 mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, EpiParams P) {
     using C = Cfg<BN>;
+    constexpr int ST = C::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* tiles = smem;
-    uint64_t* bars = (uint64_t*)(smem + C::STAGES * C::STAGE);      // full[STAGES], empty[STAGES], acc
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * C::STAGES + 1);
+    uint64_t* bars = (uint64_t*)(smem + ST * C::STAGE);   // full[ST], empty[ST], acc_full[2], acc_empty[2], drain
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * ST + 5);
     int* abort_flag = (int*)(tmem_slot + 1);
+    __shared__ float s_bias[MAX_EPI_COLS], s_osc[MAX_EPI_COLS], s_osh[MAX_EPI_COLS];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // N tiles of one row block are adjacent CTAs, so the A tile is re-read from L2
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = P.nk;
-    // per-column epilogue constants of this tile, staged once (zero beyond N)
-    __shared__ float s_bias[BN], s_osc[BN], s_osh[BN];
-    for (int j = threadIdx.x; j < BN; j += NTHREADS) {
-        const int c = n0 + j;
-        const bool in = c < P.N;
-        s_bias[j] = (in && P.bias) ? P.bias[c] : 0.f;
-        s_osc[j] = (in && P.oscale) ? P.oscale[c] : 1.f;
-        s_osh[j] = (in && P.oshift) ? P.oshift[c] : 0.f;
+    const int ntn = (P.N + BN - 1) / BN, ntm = (P.M + BM - 1) / BM, ntiles = ntn * ntm;
+    for (int j = threadIdx.x; j < MAX_EPI_COLS; j += NTHREADS) {
+        const bool in = j < P.N;
+        s_bias[j] = (in && P.bias) ? P.bias[j] : 0.f;
+        s_osc[j] = (in && P.oscale) ? P.oscale[j] : 1.f;
+        s_osh[j] = (in && P.oshift) ? P.oshift[j] : 0.f;
     }
-
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + ST);
+    const uint32_t accf0 = smem_u32(bars + 2 * ST), acce0 = smem_u32(bars + 2 * ST + 2);
+    const uint32_t drain = smem_u32(bars + 2 * ST + 4);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * C::STAGES + 1; ++s) mbar_init(smem_u32(bars + s), 1);
+        for (int s = 0; s < 2 * ST + 2; ++s) mbar_init(smem_u32(bars + s), 1);
+        mbar_init(acce0, EPI_WARPS);
+        mbar_init(acce0 + 8, EPI_WARPS);
+        mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 2) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)C::TMEM_COLS)
+                     "r"((uint32_t)(2 * C::TMEM_COLS))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -291,80 +309,102 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t acc_bar = smem_u32(bars + 2 * C::STAGES);
+    volatile int* abort_v = abort_flag;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % C::STAGES;
-            if (kb >= C::STAGES && !mbar_wait(smem_u32(bars + C::STAGES + s), ((kb / C::STAGES) - 1) & 1)) {
-                atomicOr(P.err, 1);
-                *(volatile int*)abort_flag = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer over all tiles of this CTA
+            long long g = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x) {
+                const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % ST);
+                    if (g >= ST && !mbar_wait(empty0 + 8 * s, (uint32_t)(((g / ST) - 1) & 1))) {
+                        atomicOr(P.err, 1);
+                        *abort_v = 1;
+                    }
+                    if (*abort_v) break;
+                    const uint32_t sa = smem_u32(tiles + s * C::STAGE);
+                    mbar_expect_tx(full0 + 8 * s, C::STAGE);
+                    tma_load_2d(sa, &mapA, full0 + 8 * s, kb * BK, m0);
+                    tma_load_2d(sa + C::A_BYTES, &mapB, full0 + 8 * s, kb * BK, n0);
+                }
             }
-            if (*(volatile int*)abort_flag) break;
-            const uint32_t full = smem_u32(bars + s);
-            const uint32_t sa = smem_u32(tiles + s * C::STAGE);
-            mbar_expect_tx(full, C::STAGE);
-            tma_load_2d(sa, &mapA, full, kb * BK, m0);
-            tma_load_2d(sa + C::A_BYTES, &mapB, full, kb * BK, n0);
-            ++issued;
+            if (*abort_v)   // let the copies still in flight land before the CTA exits
+                for (long long h = g - 1; h >= 0 && h >= g - ST; --h)
+                    mbar_wait(full0 + 8 * (int)(h % ST), (uint32_t)((h / ST) & 1));
         }
-        if (*(volatile int*)abort_flag) {
-            // let the copies still in flight land before the CTA exits
-            for (int kb = issued - 1; kb >= 0 && kb >= issued - C::STAGES; --kb)
-                mbar_wait(smem_u32(bars + kb % C::STAGES), (kb / C::STAGES) & 1);
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            long long g = 0;
+            int u = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_v; t += gridDim.x, ++u) {
+                const int b = u & 1, q = u >> 1;
+                if (q >= 1 && !mbar_wait(acce0 + 8 * b, (uint32_t)((q - 1) & 1))) {
+                    atomicOr(P.err, 8);
+                    *abort_v = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * C::TMEM_COLS);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % ST);
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)((g / ST) & 1)) || *abort_v) {
+                        atomicOr(P.err, 2);
+                        *abort_v = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(tiles + s * C::STAGE);
+                    const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(acc, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc, (kb | k) != 0);
+                    mma_commit(empty0 + 8 * s);        // frees the stage once these MMAs are done
+                }
+                if (*abort_v) break;
+                mma_commit(accf0 + 8 * b);             // accumulator b complete
+            }
+            mma_commit(drain);                         // every MMA this thread issued has completed
+            if (!mbar_wait(drain, 0)) atomicOr(P.err, 16);
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN);
-        int done = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % C::STAGES;
-            if (!mbar_wait(smem_u32(bars + s), (kb / C::STAGES) & 1) || *(volatile int*)abort_flag) {
-                atomicOr(P.err, 2);
-                *(volatile int*)abort_flag = 1;
+    } else {
+        // epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 and one column group
+        const int lg = warp & 3, grp = (warp - 2) >> 2;
+        constexpr int NCH = BN / 16;                   // 16-column chunks of a tile
+        const int c_lo = 16 * (grp * NCH / EPI_GROUPS), c_hi = 16 * ((grp + 1) * NCH / EPI_GROUPS);
+        int u = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++u) {
+            const int b = u & 1, q = u >> 1;
+            const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+            const bool ok = !*abort_v && mbar_wait(accf0 + 8 * b, (uint32_t)(q & 1));
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicOr(P.err, 4);
+                *abort_v = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(tiles + s * C::STAGE);
-            const uint32_t sb = sa + C::A_BYTES;
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-                mma_bf16(tmem, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), idesc, (kb | k) != 0);
-            mma_commit(smem_u32(bars + C::STAGES + s));          // frees the stage once these MMAs are done
-            ++done;
-        }
-        mma_commit(acc_bar);                                       // accumulator complete (or drained)
-        (void)done;
-    }
-    __syncwarp();
-
-    // epilogue: all four warps
-    const bool acc_ok = mbar_wait(acc_bar, 0);
-    __syncwarp();
-    tc_fence_after();
-    if (!acc_ok) {
-        if (lane == 0) atomicOr(P.err, 4);
-    } else if (!*(volatile int*)abort_flag && nk > 0) {
-        // warp w may read TMEM lanes 32 (w % 4) .. + 31; warps w and w + 4 split the columns
-        const int lg = warp & 3, half = warp >> 2;
-        const int row = m0 + lg * 32 + lane;
-        const uint32_t tw = tmem + ((uint32_t)(lg * 32) << 16);
-        constexpr int CH = ((BN / 16) + 1) / 2 * 16;       // columns of the first half, multiple of 16
+            const int row = m0 + lg * 32 + lane;
+            const uint32_t tw = tmem + (uint32_t)(b * C::TMEM_COLS) + ((uint32_t)(lg * 32) << 16);
 #pragma unroll 1
-        for (int c = half * CH; c < (half ? BN : CH); c += 16) {
-            float v[16];
-            tmem_ld16(tw + c, v);
-            if (n0 + c < P.N) epilogue_chunk<EPI>(P, row, n0 + c, v, s_bias + c, s_osc + c, s_osh + c);
+            for (int c = c_lo; c < c_hi; c += 16) {
+                float v[16];
+                tmem_ld16(tw + c, v);
+                if (n0 + c < P.N) epilogue_chunk<EPI>(P, row, n0 + c, v, s_bias + n0 + c, s_osc + n0 + c, s_osh + n0 + c);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
         }
     }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (warp == 2) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)(2 * C::TMEM_COLS))
                      : "memory");
     }
 }
@@ -408,7 +448,11 @@ int launch_t(const CUtensorMap& a, const CUtensorMap& b, const EpiParams& P, int
     if (cudaFuncSetAttribute(mlp_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
         cudaSuccess)
         return FP_ECUDA;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ntiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
     mlp_gemm_kernel<BN, EPI><<<grid, NTHREADS, C::SMEM, st>>>(a, b, P);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
 }
@@ -430,6 +474,7 @@ int launch_bn(int BN, const CUtensorMap& a, const CUtensorMap& b, const EpiParam
 int gemm(int epi, int BN, const void* A, int lda, const void* B, int ldb, int M, int N, int K, const EpiParams& P_in,
          cudaStream_t st) {
     if (M < 1 || N < 1 || K < 1) return FP_EINVAL;
+    if (N > MAX_EPI_COLS && (P_in.bias || P_in.oscale || P_in.oshift)) return FP_EINVAL;
     CUtensorMap ma, mb;
     int rc = make_map(&ma, A, M, K, lda, BM);
     if (rc != FP_OK) return rc;
