@@ -61,6 +61,23 @@ __host__ __device__ inline int nblk(int mu, int L) { return mu == 0 ? L + 1 : 2 
 __host__ __device__ inline int ldb(int n) { return n | 1; }
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Step-control constants of the forward integration (defaults of this build):
+// the Newton iteration stops when eta * |dZ| <= FP_KAPPA * tolerance; factors
+// are reused while h / h_factor stays in [FP_HRAT_LO, FP_HRAT_HI] and are
+// refreshed after a step whose contraction rate exceeded FP_THETA_REFAC.
+#ifndef FP_KAPPA
+#define FP_KAPPA 0.1f
+#endif
+#ifndef FP_THETA_REFAC
+#define FP_THETA_REFAC 0.1f
+#endif
+#ifndef FP_HRAT_LO
+#define FP_HRAT_LO 0.8
+#endif
+#ifndef FP_HRAT_HI
+#define FP_HRAT_HI 1.25
+#endif
+
 struct Layout {
     int N, L, nmax;
     size_t y, Z, F, f0, yb, diag, rr, zr, rc, zc, dnv, upv, fr, fc, Xr, Xc, lam, aw, ic, total;
@@ -876,7 +893,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         const bool last = nrem <= 1.0;
         const double hs = last ? rem : rem / nrem;
         const double rat = fac_valid ? hs / h_f : 0.0;
-        if (!fac_valid || force_refac || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
+        if (!fac_valid || force_refac || rat < FP_HRAT_LO || rat > FP_HRAT_HI || since_fac >= A.tol.refactor_every) {
             refactor<S>(C, A, P, R, off, t, hs, sh);
             h_f = hs; fac_valid = true; force_refac = false; since_fac = 0; ++out.nfac;
         }
@@ -887,7 +904,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         stage_scalars<S>(A, P, R, off, t, hs, have_pred, h_old, sh);
         predict_stages<S>(C, have_pred, sh);
         const double sc_err = atol + rtol * ymax;
-        const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_err, eta, 0.02f, A.tol.newton_max_iter, sh);
+        const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_err, eta, FP_KAPPA, A.tol.newton_max_iter, sh);
         out.nit += nr.iters;
         if (nr.nonfinite) { out.status = FP_STATUS_NONFINITE; break; }
         if (!nr.conv) {
@@ -898,7 +915,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
             __syncthreads();
             continue;
         }
-        if (nr.theta > 0.1f) force_refac = true;   // slow contraction: refresh the factors next step
+        if (nr.theta > FP_THETA_REFAC) force_refac = true;   // slow contraction: refresh the factors next step
         // embedded error estimate, filtered through the real factor
         for (int b = threadIdx.x; b < N; b += NT) {
             const int i = __ldg(C.glob + b);
