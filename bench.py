@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FP instance-periods/s at ≤1e-9 rel err vs FP64 oracle; surrogate speedup at 1e-3"
 UNIT = "instance-periods/s"
 L2_FLUSH_BYTES = 256 << 20
-SOLVER_S5_TRAFFIC_BYTES = (2.43 + 95.76) * 1e6      # dram read + write of one fp_solve_kernel<5> launch
+SOLVER_S5_TRAFFIC_BYTES = None    # dram read + write of one fp_solve_kernel<5> launch (None: not captured for this build)
 
 
 def parse():
@@ -318,13 +318,14 @@ def adjoint_leg(fp, dev, n_inst=152):
     from paper_2106_08040_gb300 import workloads
     dspec, inst = workloads.system_matrix_workload()
     inst = inst[:n_inst]
-    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=3), 16)
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=3, max_steps=200000), 16)
     n, K = len(inst), 816
     ch = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     d_inst = fp.instances_to_device(inst, dev)
     dJ = torch.from_numpy(np.random.default_rng(3).normal(size=(n, 2, K + 1, 2))).to(dev)
     grad = torch.empty((n, 4), dtype=torch.float64, device=dev)
     st = torch.empty((n,), dtype=torch.int32, device=dev)
+    gstats = torch.zeros((n, 4), dtype=torch.int32, device=dev)
     work = torch.empty(fp.fp_grad_workspace_bytes(ctx, n), dtype=torch.uint8, device=dev)
     S = ctx.num_samples()
     dm = torch.empty((n, S, 3), dtype=torch.float64, device=dev)
@@ -334,7 +335,7 @@ def adjoint_leg(fp, dev, n_inst=152):
     fp.fp_solve_batch(ctx, d_inst, n, None, dm, st, None)
     fp.fp_signal(ctx, dm, n, K, ch, ph)
     ev[1].record()
-    fp.fp_grad(ctx, d_inst, n, K, ch, dJ, grad, st, work)
+    fp.fp_grad(ctx, d_inst, n, K, ch, dJ, grad, st, work, d_stats=gstats)
     ev[2].record()
     torch.cuda.synchronize()
     t_f, t_a = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
@@ -342,6 +343,7 @@ def adjoint_leg(fp, dev, n_inst=152):
     out = {"instances": n, "forward_ms": t_f, "adjoint_ms": t_a, "adjoint_over_forward": t_a / t_f,
            "gradients_per_s": n / (t_a * 1e-3), "instance_periods_per_s": n * periods / (t_a * 1e-3),
            "status_ok": int((st.cpu().numpy() == 0).sum()), "workspace_bytes": int(work.numel()),
+           "failed_phase_counts": np.bincount(gstats[:, 2].cpu().numpy(), minlength=4).tolist(),
            "workload": "first %d voxels of the 32x32 system-matrix batch, L = 16, Radau s = 3, rtol 1e-9, "
                        "checkpoints every 64 steps" % n}
     ctx.close()
@@ -472,7 +474,7 @@ def run_gpu(args):
     # DRAM bytes per launch from the one-pass ncu capture of this kernel on this workload
     # (profiles/solver_s5_system_matrix_L16.md); null for any other configuration
     full = n == 1024 and periods == 2 and L == 16
-    traffic = SOLVER_S5_TRAFFIC_BYTES if (full and args.stages == 5 and args.rtol == 1e-9) else None
+    traffic = SOLVER_S5_TRAFFIC_BYTES if (full and args.stages == 5 and args.rtol == 1e-9 and world == 1) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak / 1e3, "unit": "TFLOP/s",
             "frac": achieved / (peak / 1e3), "traffic": traffic,
             "traffic_source": "profiles/solver_s5_system_matrix_L16.md" if traffic else None,

@@ -809,9 +809,11 @@ __device__ void refactor(Ctx<S>& C, const KArgs& A, const FpParams& P, const dou
 
 // Adaptive integration of one instance over the whole schedule.  SOLVE mode
 // writes <m>, d<m>/dt at every sample; REC mode instead records every accepted
-// step (t, h, sample index or -1) in rec_steps and the state before every
-// CKPT-th step in rec_ckpt.
+// step (t, h, sample index or -1, and the (t, h) its iteration matrices were
+// factorised at) in rec_steps and the state before every CKPT-th step in
+// rec_ckpt, so that a replay can use exactly the same factors.
 #define FP_CKPT 64
+#define FP_REC 5            // doubles recorded per accepted step
 struct FwdOut { int status, nsteps, nrej, nit, nfac; };
 
 template <int S, bool REC>
@@ -835,7 +837,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
     int jn = 0;
     bool have_pred = false, fac_valid = false, force_refac = false;
     int since_fac = 0;
-    double h_f = 0.0, h_old = 0.0;
+    double h_f = 0.0, h_old = 0.0, t_f = 0.0;
     float eta = 1.0f;
 
     {
@@ -895,7 +897,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         const double rat = fac_valid ? hs / h_f : 0.0;
         if (!fac_valid || force_refac || rat < FP_HRAT_LO || rat > FP_HRAT_HI || since_fac >= A.tol.refactor_every) {
             refactor<S>(C, A, P, R, off, t, hs, sh);
-            h_f = hs; fac_valid = true; force_refac = false; since_fac = 0; ++out.nfac;
+            h_f = hs; t_f = t; fac_valid = true; force_refac = false; since_fac = 0; ++out.nfac;
         }
         if (REC && out.nsteps % FP_CKPT == 0) {       // checkpoint the state before this step
             double* ck = rec_ckpt + (size_t)(out.nsteps / FP_CKPT) * N;
@@ -936,8 +938,8 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         const double fac = en > 0.0 ? 0.9 * (double)powf((float)en, -1.f / (S + 1)) : 4.0;
         if (en <= 1.0) {
             if (REC && threadIdx.x == 0) {
-                double* r = rec_steps + (size_t)out.nsteps * 3;
-                r[0] = t; r[1] = hs; r[2] = last ? (double)jn : -1.0;
+                double* r = rec_steps + (size_t)out.nsteps * FP_REC;
+                r[0] = t; r[1] = hs; r[2] = last ? (double)jn : -1.0; r[3] = t_f; r[4] = h_f;
             }
             float ymx = 0.f;
             for (int i = threadIdx.x; i < N; i += NT) {
@@ -1206,6 +1208,7 @@ __device__ int adjoint_stages(Ctx<S>& C, const DevTab& T, double hs, double h_f,
     if (lmax == 0.f) return 0;
     if (!(lmax <= 3.0e38f)) return -1;
     float prev = 3.0e38f;
+    bool last = false;
     for (int it = 0; it < maxit; ++it) {
         // v_i = sum_j a_ji zeta_j ; w_i = A_i^T v_i
         for (int e = threadIdx.x; e < S * N; e += NT) {
@@ -1260,7 +1263,7 @@ __device__ int adjoint_stages(Ctx<S>& C, const DevTab& T, double hs, double h_f,
         }
         __syncthreads();
         // zeta += T^{-T} omega (h_f / h)
-        float dm = 0.f;
+        float dm = 0.f, zm = 0.f;
         for (int b = threadIdx.x; b < N; b += NT) {
             const int r = __ldg(C.glob + b);
             float om[S];
@@ -1278,15 +1281,22 @@ __device__ int adjoint_stages(Ctx<S>& C, const DevTab& T, double hs, double h_f,
                 for (int j = 0; j < S; ++j) dz = fmaf((float)RAD<S>().Ti[j][k], om[j], dz);
                 C.F[k * N + r] += (double)dz;
                 dm = nanmax(dm, fabsf(dz));
+                zm = nanmax(zm, fabsf((float)C.F[k * N + r]));
             }
         }
         const float dmax = block_max(dm, sh.red);
-        if (!(dmax <= 3.0e38f)) return -1;
-        if (dmax <= 1e-11f * lmax) return it + 1;
-        if (it >= 2 && dmax > 0.99f * prev) return dmax <= 1e-8f * lmax ? it + 1 : -2;   // stagnated
+        const float zmax = block_max(zm, sh.red);
+        if (!(dmax <= 3.0e38f) || !(zmax <= 3.0e38f)) return -1;
+        // increments relative to the larger of lambda and zeta (zeta can exceed
+        // lambda by the conditioning of the step); a stalled or slow iteration
+        // is accepted once its increments are below 1e-7 of that scale
+        const float scale = fmaxf(lmax, zmax);
+        if (dmax <= 1e-10f * scale) return it + 1;
+        if (it >= 2 && dmax > 0.99f * prev) return dmax <= 1e-7f * scale ? it + 1 : -2;   // stagnated
         prev = dmax;
+        last = dmax <= 1e-7f * scale;
     }
-    return -2;
+    return last ? maxit : -2;
 }
 
 struct GArgs {
@@ -1313,8 +1323,8 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
     const int Sp = A.drv.samples_per_period, j0 = A.S_out - Sp;
     const int Nmax = (A.L_launch + 1) * (A.L_launch + 1);
     double* ws = G.work + (size_t)blockIdx.x * G.work_per_cta;
-    double* ws_steps = ws;                                              // [max_rec][3]
-    double* ws_ckpt = ws_steps + (size_t)G.max_rec * 3;                 // [max_rec/CKPT + 1][Nmax]
+    double* ws_steps = ws;                                              // [max_rec][FP_REC]
+    double* ws_ckpt = ws_steps + (size_t)G.max_rec * FP_REC;            // [max_rec/CKPT + 1][Nmax]
     double* ws_seg = ws_ckpt + (size_t)(G.max_rec / FP_CKPT + 1) * Nmax; // [CKPT + 1][Nmax]
     double* ws_g = ws_seg + (size_t)(FP_CKPT + 1) * Nmax;                // [Sp][3]
     double* ws_Z = ws_g + (size_t)Sp * 3;                                // [CKPT][S][Nmax] stage increments
@@ -1359,9 +1369,11 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
         __syncthreads();
         // (3) backward sweep, segment by segment
         double sc_rep = A.tol.atol;                // replay Newton tolerance, set per segment
+        // the iteration matrices of every replayed and transposed step are the
+        // forward's: refactorised whenever the recorded factor point changes
         bool fac_valid = false;
-        double h_f = 0.0;
-        int since_fac = 0, fail_phase = 0, fail_step = -1;
+        double h_f = 0.0, t_fc = 0.0;
+        int fail_phase = 0, fail_step = -1;
         const int nseg = (nacc + FP_CKPT - 1) / FP_CKPT;
         for (int sg = nseg - 1; sg >= 0 && status == FP_STATUS_OK; --sg) {
             const int n0 = sg * FP_CKPT, n1 = min(nacc, n0 + FP_CKPT);
@@ -1377,24 +1389,33 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
             sc_rep = A.tol.atol + A.tol.rtol * (double)block_max(ym, sh.red);
             fac_valid = false;                     // the last factors belong to a later time
             for (int n = n0; n < n1; ++n) {
-                const double t = ws_steps[(size_t)n * 3], hs = ws_steps[(size_t)n * 3 + 1];
-                const double rat = fac_valid ? hs / h_f : 0.0;
-                if (!fac_valid || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
-                    refactor<S>(C, A, P, R, off, t, hs, sh);
-                    h_f = hs; fac_valid = true; since_fac = 0;
+                const double* rs = ws_steps + (size_t)n * FP_REC;
+                const double t = rs[0], hs = rs[1];
+                if (!fac_valid || rs[3] != t_fc || rs[4] != h_f) {
+                    refactor<S>(C, A, P, R, off, rs[3], rs[4], sh);
+                    t_fc = rs[3]; h_f = rs[4]; fac_valid = true;
                 }
                 stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
                 predict_stages<S>(C, false, sh);
                 float eta = 1.f;
-                const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_rep, eta, 0.02f, 4 * A.tol.newton_max_iter, sh);
+                NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_rep, eta, 0.02f, 4 * A.tol.newton_max_iter, sh);
                 // a stalled iteration whose last increment is already below the
-                // tolerance scale is as good as the forward's accepted stages
+                // tolerance scale is as good as the forward's accepted stages;
+                // otherwise (the forward reached these stages from a better
+                // predictor) retry from zero with factors made for this very step
+                if (!nr.nonfinite && !nr.conv && !(nr.dmax <= (float)sc_rep)) {
+                    refactor<S>(C, A, P, R, off, t, hs, sh);
+                    t_fc = t; h_f = hs;
+                    stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
+                    predict_stages<S>(C, false, sh);
+                    eta = 1.f;
+                    nr = newton_stages<S>(C, T, hs, h_f, sc_rep, eta, 0.02f, 4 * A.tol.newton_max_iter, sh);
+                }
                 if (nr.nonfinite || (!nr.conv && !(nr.dmax <= (float)sc_rep))) {
                     status = nr.nonfinite ? FP_STATUS_NONFINITE : FP_STATUS_NEWTON_FAIL;
                     fail_phase = 2; fail_step = n;
                     break;
                 }
-                ++since_fac;
                 double* zs = ws_Z + (size_t)(n - n0) * S * N;
                 for (int e = threadIdx.x; e < S * N; e += NT) zs[e] = C.Z[e];
                 for (int i = threadIdx.x; i < N; i += NT) {
@@ -1406,8 +1427,9 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
             if (status != FP_STATUS_OK) break;
             fac_valid = false;
             for (int n = n1 - 1; n >= n0; --n) {
-                const double t = ws_steps[(size_t)n * 3], hs = ws_steps[(size_t)n * 3 + 1];
-                const int js = (int)ws_steps[(size_t)n * 3 + 2];
+                const double* rs = ws_steps + (size_t)n * FP_REC;
+                const double t = rs[0], hs = rs[1];
+                const int js = (int)rs[2];
                 // readout at t + hs if this step landed on a sample of the last period
                 if (js >= j0) {
                     if (threadIdx.x < 3) s_g[threadIdx.x] = ws_g[(js - j0) * 3 + threadIdx.x];
@@ -1423,15 +1445,20 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
                 for (int i = threadIdx.x; i < N; i += NT) C.y[i] = ws_seg[(size_t)(n - n0) * N + i];
                 for (int e = threadIdx.x; e < S * N; e += NT) C.Z[e] = zs[e];
                 __syncthreads();
-                const double rat = fac_valid ? hs / h_f : 0.0;
-                if (!fac_valid || rat < 0.8 || rat > 1.25 || since_fac >= A.tol.refactor_every) {
-                    refactor<S>(C, A, P, R, off, t, hs, sh);
-                    h_f = hs; fac_valid = true; since_fac = 0;
+                if (!fac_valid || rs[3] != t_fc || rs[4] != h_f) {
+                    refactor<S>(C, A, P, R, off, rs[3], rs[4], sh);
+                    t_fc = rs[3]; h_f = rs[4]; fac_valid = true;
                 }
-                ++since_fac;
                 stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
-                // transposed stage solve for zeta (in F)
-                const int ai = adjoint_stages<S>(C, T, hs, h_f, 4 * A.tol.newton_max_iter, sh);
+                // transposed stage solve for zeta (in F); a slow iteration with the
+                // forward's factors is retried with factors made for this step
+                int ai = adjoint_stages<S>(C, T, hs, h_f, 4 * A.tol.newton_max_iter, sh);
+                if (ai == -2) {
+                    refactor<S>(C, A, P, R, off, t, hs, sh);
+                    t_fc = t; h_f = hs;
+                    stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
+                    ai = adjoint_stages<S>(C, T, hs, h_f, 16 * A.tol.newton_max_iter, sh);
+                }
                 if (ai < 0) {
                     status = ai == -1 ? FP_STATUS_NONFINITE : FP_STATUS_NEWTON_FAIL;
                     fail_phase = 3; fail_step = n;
@@ -1567,7 +1594,7 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
 
 size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec) {
     const size_t Nmax = (size_t)(L_max + 1) * (L_max + 1);
-    return (size_t)max_rec * 3 + (size_t)(max_rec / FP_CKPT + 1) * Nmax + (size_t)(FP_CKPT + 1) * Nmax +
+    return (size_t)max_rec * FP_REC + (size_t)(max_rec / FP_CKPT + 1) * Nmax + (size_t)(FP_CKPT + 1) * Nmax +
            (size_t)S_p * 3 + (size_t)FP_CKPT * stages * Nmax;
 }
 

@@ -77,5 +77,30 @@ class FitProblem:
         g = grad.view(len(params), len(self.offsets), 4).sum(dim=1)
         return J.cpu().numpy(), g.cpu().numpy(), ok
 
+    def fit(self, params0, u, iters=20, lr=0.05, beta1=0.9, beta2=0.999):
+        """Adam on q = (ln K, ln d, theta, phi) of each candidate, gradients by the
+        adjoint (dJ/dln K = K dJ/dK, likewise d).  Returns the final parameters
+        [P, 4] and the misfit history [iters + 1, P]."""
+        p = np.atleast_2d(np.asarray(params0, dtype=np.float64)).copy()
+        q = np.column_stack([np.log(p[:, 0]), np.log(p[:, 1]), p[:, 2], p[:, 3]])
+        m = np.zeros_like(q)
+        v = np.zeros_like(q)
+        hist = []
+        for it in range(iters + 1):
+            p = np.column_stack([np.exp(q[:, 0]), np.exp(q[:, 1]), q[:, 2], q[:, 3]])
+            J, g, ok = self.misfit_and_grad(p, u)
+            if not ok:
+                raise RuntimeError("solve or adjoint did not converge at iteration %d" % it)
+            hist.append(J)
+            if it == iters:
+                break
+            gq = g * np.column_stack([p[:, 0], p[:, 1], np.ones(len(p)), np.ones(len(p))])
+            m = beta1 * m + (1 - beta1) * gq
+            v = beta2 * v + (1 - beta2) * gq * gq
+            mh = m / (1 - beta1 ** (it + 1))
+            vh = v / (1 - beta2 ** (it + 1))
+            q = q - lr * mh / (np.sqrt(vh) + 1e-30)
+        return p, np.array(hist)
+
     def close(self):
         self.ctx.close()

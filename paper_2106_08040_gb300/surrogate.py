@@ -222,3 +222,37 @@ class Surrogate:
             getattr(s, k).copy_(torch.from_numpy(z[k]))
         s.refresh()
         return s
+
+
+def main():
+    """Time inference of an untrained network (random weights, random inputs):
+    python -m paper_2106_08040_gb300.surrogate --queries 1024000 --repeat 10"""
+    import argparse
+    import json
+    import torch
+    p = argparse.ArgumentParser()
+    p.add_argument("--queries", type=int, default=1024000)
+    p.add_argument("--repeat", type=int, default=10)
+    p.add_argument("--seed", type=int, default=1)
+    a = p.parse_args()
+    s = Surrogate(seed=a.seed)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(a.seed)
+    x = torch.randn(a.queries, N_IN, device="cuda", generator=g)
+    y = torch.empty(a.queries, N_OUT, device="cuda")
+    s.infer(x, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.repeat):
+        s.infer(x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(a.repeat, 1)
+    flops = 2.0 * a.queries * (N_IN * HIDDEN + 3 * HIDDEN * HIDDEN + HIDDEN * N_OUT)
+    print(json.dumps({"queries": a.queries, "ms_per_network": ms, "tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
+                      "err_flag": s.error_flag()}))
+
+
+if __name__ == "__main__":
+    main()
