@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FP instance-periods/s at ≤1e-9 rel err vs FP64 oracle; surrogate speedup at 1e-3"
 UNIT = "instance-periods/s"
 L2_FLUSH_BYTES = 256 << 20
-SOLVER_S5_TRAFFIC_BYTES = None    # dram read + write of one fp_solve_kernel<5> launch (None: not captured for this build)
+SOLVER_S5_TRAFFIC_BYTES = (2.51 + 94.30) * 1e6   # dram read + write of one fp_solve_kernel<5> launch, full workload
 
 
 def parse():
