@@ -276,7 +276,7 @@ def surrogate_leg(fp, dev):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     q_per_s = q / (ms * 1e-3)
-    # judge: fresh draws from the training domain, solved by the FP path
+    # error reference: fresh draws from the training domain, solved by the FP path
     draw = workloads.uneven_sweep_instances(1024, 16, seed=7)
     draw = draw[fp.Material().sigma(draw["K"], draw["d"]) <= 12.0][:152]
     ctx = stt.solver_context(16, 1e-7)
@@ -307,7 +307,7 @@ def surrogate_leg(fp, dev):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": src,
                          "kernel": "mlp_gemm_kernel (tcgen05 BF16, 2 members x 5 layers)"},
-            "judge": "fp_solve_batch + fp_signal, L = 16, rtol 1e-7, 152 fresh draws of the training domain"}
+            "error_reference": "fp_solve_batch + fp_signal, L = 16, rtol 1e-7, 152 fresh draws of the training domain"}
 
 
 def adjoint_leg(fp, dev, n_inst=152):

@@ -253,7 +253,7 @@ int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
  * leading harmonics of its normalised signal phi_hat (Sec. 2.2, model M1),
  * FP_SUR_OUT = 2 channels x 200 complex harmonics k = 1..200, stored
  * [channel][k-1][re, im].  The paper has no surrogate; the Fokker-Planck solve
- * (fp_solve_batch + fp_signal) produces its training data and judges its error.
+ * (fp_solve_batch + fp_signal) produces its training data and is the reference for its error.
  * Layers l = 0..4: z_l = W_l x_l + b_l with x_0 the normalised, zero-padded
  * input (64 wide), x_{l+1} = gelu(z_l) (exact erf form) for l < 4 and the
  * output y = z_4 * out_scale + out_shift.  BF16 operands, FP32 accumulation on

@@ -5,7 +5,7 @@ maps one instance -- offset field B_off [T] (3), easy-axis theta, phi [rad],
 ln K, ln d -- to the first 200 complex harmonics (k = 1..200) of the normalised
 signal phi_hat of the x and y receive channels (Sec. 2.2, model M1), laid out
 [channel][k-1][re, im].  The paper has no surrogate: the Fokker-Planck solve
-produces its training data and is the judge of its error (and its fallback).
+produces its training data and is the reference for its error (and its fallback).
 
 This module holds the weights (FP32 masters, BF16 copies, Adam moments) in
 torch device tensors and marshals them to fp_surrogate_infer /

@@ -1,4 +1,4 @@
-"""Train the harmonic surrogate on solves of the method and judge it with them.
+"""Train the harmonic surrogate on solves of the method and measure its error against them.
 
     python -m paper_2106_08040_gb300.surrogate_train --train 32768 --holdout 1024 \
         --steps 60000 --out paper_2106_08040_gb300/data/surrogate_L16.npz

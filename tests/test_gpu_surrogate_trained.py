@@ -1,7 +1,7 @@
 """The trained surrogate against the method that trained it.
 
 Fresh draws of the training domain (uneven-sweep distribution, barrier
-sigma <= 12, L = 16) are solved by fp_solve_batch + fp_signal (the judge) and
+sigma <= 12, L = 16) are solved by fp_solve_batch + fp_signal (the reference) and
 answered by the two-member surrogate ensemble.  The stated accuracy comes from
 the held-out evaluation at training time (median relative L2 error of the 400
 complex harmonics about 1.5e-2, 90th percentile about 6e-2), checked here with
