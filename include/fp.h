@@ -216,7 +216,10 @@ long long fp_grad_workspace_bytes(const fp_ctx* ctx, int n);
  * none).  Gradients of instances whose status is not FP_STATUS_OK are 0.
  * d_work: device workspace of
  * work_bytes >= fp_grad_workspace_bytes(ctx, n), owned by the caller, contents
- * undefined on return.  Asynchronous on `stream`. */
+ * undefined on return.  Asynchronous on `stream`.  The adjoint keeps one more
+ * state and stage block in shared memory than the solve: with 5 stages at
+ * L_max = 16 that exceeds the 227 KB per CTA and the call returns
+ * FP_EUNSUPPORTED (use a 3-stage context for gradients at that degree). */
 int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
             const double* h_channels, int C, const double* d_dJ_dphihat,
             double* d_grad, int* d_status, int* d_stats, void* d_work,
