@@ -180,6 +180,14 @@ int fp_signal(fp_ctx* ctx, const double* d_dmdt, int n, int k_max,
 typedef struct fp_sweep fp_sweep;
 
 int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_width, fp_sweep** out);
+/* The host part of fp_sweep_plan, without a context or a GPU: h_order[n]
+ * receives the queue order (instance indices, buckets of decreasing launch
+ * degree, each by decreasing sigma + b_T |B|max), h_bucket_L / h_bucket_count
+ * (at least FP_L_MAX_ANY entries, may be NULL) each bucket's launch degree and
+ * size, *n_buckets their number.  Instances with L outside [2, L_max] are
+ * FP_EINVAL. */
+int fp_sweep_order(const fp_material* mat, const fp_drive* drv, int L_max, const fp_instance* h_inst, int n,
+                   int bucket_width, int* h_order, int* h_bucket_L, int* h_bucket_count, int* n_buckets);
 int fp_sweep_run(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_dmdt, int* d_status,
                  int* d_stats, void* stream);
 int fp_sweep_autotune(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_dmdt, int* d_status,

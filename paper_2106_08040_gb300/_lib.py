@@ -15,7 +15,7 @@ STATUS = {0: "OK", 1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTO
 
 EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_solve_batch",
             "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_grad_noalloc", "fp_surrogate_workspace_bytes", "fp_surrogate_infer",
-            "fp_surrogate_grad", "fp_surrogate_adam", "fp_sweep_plan", "fp_sweep_run",
+            "fp_surrogate_grad", "fp_surrogate_adam", "fp_sweep_plan", "fp_sweep_order", "fp_sweep_run",
             "fp_sweep_autotune", "fp_sweep_info", "fp_sweep_destroy", "fp_operator_dense", "fp_peak_fp64",
             "fp_status_str", "fp_last_error"]
 
@@ -102,6 +102,9 @@ def lib():
     L.fp_surrogate_adam.restype = i
     L.fp_sweep_plan.argtypes = [vp, vp, i, i, C.POINTER(vp)]
     L.fp_sweep_plan.restype = i
+    L.fp_sweep_order.argtypes = [C.POINTER(fp_material), C.POINTER(fp_drive), i, vp, i, i, C.POINTER(i), C.POINTER(i),
+                                 C.POINTER(i), C.POINTER(i)]
+    L.fp_sweep_order.restype = i
     L.fp_sweep_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.fp_sweep_run.restype = i
     L.fp_sweep_autotune.argtypes = [vp, vp, vp, vp, vp, i, vp]

@@ -102,43 +102,61 @@ int enqueue_all(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_
 
 extern "C" {
 
-int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_width, fp_sweep** out) {
-    if (!ctx || !h_inst || !out) return fp_fail(FP_EINVAL, "fp_sweep_plan: NULL argument");
-    *out = nullptr;
-    if (n < 1) return fp_fail(FP_EINVAL, "fp_sweep_plan: n=%d", n);
-    if (bucket_width < 1) return fp_fail(FP_EINVAL, "fp_sweep_plan: bucket_width=%d", bucket_width);
-    const double kT = 1.380649e-23 * ctx->mat.T_B;
-    const double amp = std::sqrt(ctx->drv.amp[0] * ctx->drv.amp[0] + ctx->drv.amp[1] * ctx->drv.amp[1] +
-                                 ctx->drv.amp[2] * ctx->drv.amp[2]);
+int fp_sweep_order(const fp_material* mat, const fp_drive* drv, int L_max, const fp_instance* h_inst, int n,
+                   int bucket_width, int* h_order, int* h_bucket_L, int* h_bucket_count, int* n_buckets) {
+    if (!mat || !drv || !h_inst || !h_order || !n_buckets) return fp_fail(FP_EINVAL, "fp_sweep_order: NULL argument");
+    if (n < 1) return fp_fail(FP_EINVAL, "fp_sweep_order: n=%d", n);
+    if (bucket_width < 1) return fp_fail(FP_EINVAL, "fp_sweep_order: bucket_width=%d", bucket_width);
+    if (L_max < 2 || L_max > FP_L_MAX_ANY) return fp_fail(FP_EINVAL, "fp_sweep_order: L_max=%d", L_max);
+    const double kT = 1.380649e-23 * mat->T_B;
+    const double amp = std::sqrt(drv->amp[0] * drv->amp[0] + drv->amp[1] * drv->amp[1] + drv->amp[2] * drv->amp[2]);
     std::vector<int> Lb(n);
     std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {
         const fp_instance& in = h_inst[i];
-        if (in.L < 2 || in.L > ctx->L_max)
-            return fp_fail(FP_EINVAL, "fp_sweep_plan: instance %d has L=%d outside [2, %d]", i, in.L, ctx->L_max);
-        Lb[i] = std::min(ctx->L_max, (in.L + bucket_width - 1) / bucket_width * bucket_width);
+        if (in.L < 2 || in.L > L_max)
+            return fp_fail(FP_EINVAL, "fp_sweep_order: instance %d has L=%d outside [2, %d]", i, in.L, L_max);
+        Lb[i] = std::min(L_max, (in.L + bucket_width - 1) / bucket_width * bucket_width);
         const double V = 3.14159265358979323846 * in.d * in.d * in.d / 6.0;
-        const double sigma = in.K * V / kT, bT = V * ctx->mat.Ms / kT;
+        const double sigma = in.K * V / kT, bT = V * mat->Ms / kT;
         const double hb = std::sqrt(in.h_off[0] * in.h_off[0] + in.h_off[1] * in.h_off[1] + in.h_off[2] * in.h_off[2]);
         cost[i] = std::isfinite(sigma + bT * (hb + amp)) ? sigma + bT * (hb + amp) : 0.0;
     }
-    fp_sweep* sw = new (std::nothrow) fp_sweep();
-    if (!sw) return fp_fail(FP_ENOMEM, "fp_sweep_plan: host allocation");
-    sw->ctx = ctx;
-    sw->n = n;
     std::vector<int> idx(n);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
         if (Lb[a] != Lb[b]) return Lb[a] > Lb[b];
         return cost[a] > cost[b];
     });
-    sw->h_order = idx;
+    int nb = 0;
     for (int s = 0; s < n;) {
         int e = s;
         while (e < n && Lb[idx[e]] == Lb[idx[s]]) ++e;
-        sw->b.push_back(FpBucket{Lb[idx[s]], s, e - s, ctx->tol.stages, ctx->tol.refactor_every, 0.f});
+        if (h_bucket_L) h_bucket_L[nb] = Lb[idx[s]];
+        if (h_bucket_count) h_bucket_count[nb] = e - s;
+        ++nb;
         s = e;
     }
+    std::copy(idx.begin(), idx.end(), h_order);
+    *n_buckets = nb;
+    return FP_OK;
+}
+
+int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_width, fp_sweep** out) {
+    if (!ctx || !h_inst || !out) return fp_fail(FP_EINVAL, "fp_sweep_plan: NULL argument");
+    *out = nullptr;
+    if (n < 1) return fp_fail(FP_EINVAL, "fp_sweep_plan: n=%d", n);
+    std::vector<int> idx(n);
+    int bL[FP_L_MAX_ANY], bc[FP_L_MAX_ANY], nbk = 0;
+    int rc0 = fp_sweep_order(&ctx->mat, &ctx->drv, ctx->L_max, h_inst, n, bucket_width, idx.data(), bL, bc, &nbk);
+    if (rc0 != FP_OK) return rc0;
+    fp_sweep* sw = new (std::nothrow) fp_sweep();
+    if (!sw) return fp_fail(FP_ENOMEM, "fp_sweep_plan: host allocation");
+    sw->ctx = ctx;
+    sw->n = n;
+    sw->h_order = idx;
+    for (int k = 0, s = 0; k < nbk; s += bc[k], ++k)
+        sw->b.push_back(FpBucket{bL[k], s, bc[k], ctx->tol.stages, ctx->tol.refactor_every, 0.f});
     const int nb = (int)sw->b.size();
     int rc = FP_OK;
     if (cudaMalloc(&sw->d_order, sizeof(int) * n) != cudaSuccess || cudaMalloc(&sw->d_tune, sizeof(int) * n) != cudaSuccess ||

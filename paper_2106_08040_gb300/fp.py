@@ -293,6 +293,22 @@ def truncation_degree(inst, material=None, drive=None, L_min=8, L_max=16):
     return np.clip(L, L_min, L_max)
 
 
+def sweep_order(inst: np.ndarray, material: Material, drive: Drive, L_max: int, bucket_width=1):
+    """Host-only planning of a sweep (no GPU): queue order [n] and the buckets'
+    (launch degree, size) list, as fp_sweep_plan computes them."""
+    arr = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
+    n = len(arr)
+    order = np.zeros(n, dtype=np.int32)
+    bL = (C.c_int * 64)()
+    bc = (C.c_int * 64)()
+    nb = C.c_int()
+    m, d = material.c(), drive.c()
+    check(_lib.lib().fp_sweep_order(C.byref(m), C.byref(d), int(L_max), arr.ctypes.data_as(C.c_void_p), n,
+                                    int(bucket_width), order.ctypes.data_as(C.POINTER(C.c_int)), bL, bc,
+                                    C.byref(nb)), "fp_sweep_order")
+    return order, [(bL[k], bc[k]) for k in range(nb.value)]
+
+
 class Sweep:
     """fp_sweep plan over host instance records (see include/fp.h)."""
 
