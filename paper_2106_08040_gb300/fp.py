@@ -217,6 +217,7 @@ def _autograd_function():
             ch = np.asarray(channels, dtype=np.float64).reshape(-1, 3)
             out = torch.empty((n, ch.shape[0], k_max + 1, 2), dtype=torch.float64, device=dev)
             fp_signal(fpctx, dm, n, k_max, ch, out)
+            _raise_on_status(st, "solve")
             ctx_.save_for_backward(params.detach(), h_off)
             ctx_.fpctx, ctx_.L, ctx_.k_max, ctx_.ch = fpctx, L, k_max, ch
             ctx_.status = st
@@ -232,6 +233,7 @@ def _autograd_function():
             st = torch.empty((n,), dtype=torch.int32, device=dev)
             work = torch.empty(fp_grad_workspace_bytes(ctx_.fpctx, n), dtype=torch.uint8, device=dev)
             fp_grad(ctx_.fpctx, d_inst, n, ctx_.k_max, ctx_.ch, g.contiguous().to(torch.float64), grad, st, work)
+            _raise_on_status(st, "adjoint")
             return grad.to(params.dtype), None, None, None, None, None
 
     return PhiHat
@@ -240,8 +242,20 @@ def _autograd_function():
 _PHIHAT = None
 
 
+def _raise_on_status(st, what):
+    """Fail loudly when any instance of an autograd pass did not converge."""
+    s = st.cpu().numpy()
+    if (s != 0).any():
+        bad = {_lib.STATUS.get(int(v), str(int(v))): int((s == v).sum()) for v in np.unique(s[s != 0])}
+        raise RuntimeError("phi_hat %s: %d of %d instances did not converge %s" % (what, int((s != 0).sum()), len(s), bad))
+
+
 def phi_hat(params, h_off, fpctx, L, k_max, channels):
-    """Differentiable phi_hat (torch.autograd) of the batched solve."""
+    """Differentiable phi_hat (torch.autograd) of the batched solve: params
+    [n, 4] = (K, d, theta, phi), h_off [n, 3]; the backward pass is fp_grad
+    (discrete adjoint).  Raises if any instance of either pass does not
+    converge.  At L = 16 the adjoint needs a 3-stage context (a 5-stage one
+    exceeds the shared memory of a CTA)."""
     global _PHIHAT
     if _PHIHAT is None:
         _PHIHAT = _autograd_function()
