@@ -13,7 +13,7 @@ Multi-GPU (torchrun, one rank per GPU): weak scaling, rank r solves the same
 voxel batch for easy-axis angle vartheta_r = 15 deg * r (the paper's angle set),
 no collective on the data path; barrier + max-over-ranks timing.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on
+--impl reference times the FP64 CPU oracle (the reference arm) on
 a bounded sample of the same workload on the host cores.
 """
 import argparse

@@ -53,7 +53,7 @@ extern "C" {
 #define FP_EINVAL       -1   /* bad argument (NULL, size, range)               */
 #define FP_ECUDA        -2   /* a CUDA runtime call failed                     */
 #define FP_ENOMEM       -3   /* host or device allocation failed (fp_setup)    */
-#define FP_EUNSUPPORTED -4   /* valid request outside what this build supports */
+#define FP_EUNSUPPORTED -4   /* valid request outside what the library supports  */
 
 /* ---- per-instance status codes (d_status) ------------------------------- */
 #define FP_STATUS_OK             0
@@ -118,7 +118,7 @@ typedef struct {
 
 typedef struct fp_ctx fp_ctx;
 
-/* Largest truncation degree this build supports. */
+/* Largest truncation degree the library supports. */
 int fp_max_degree(void);
 
 /* Create a context: copies the material, drive and tolerances, builds the

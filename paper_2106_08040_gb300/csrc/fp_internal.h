@@ -9,7 +9,7 @@
 #define FP_HD inline
 #endif
 
-#define FP_L_MAX 16          // largest degree with shared-memory factors in this build
+#define FP_L_MAX 16          // largest degree whose factors fit in shared memory
 #define FP_NSLOT 19          // coupling slots per target row (see slot map below)
 #define FP_NGL 128           // Gauss-Legendre nodes for the Boltzmann initial state
 

@@ -61,7 +61,7 @@ __host__ __device__ inline int nblk(int mu, int L) { return mu == 0 ? L + 1 : 2 
 __host__ __device__ inline int ldb(int n) { return n | 1; }
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Step-control constants of the forward integration (defaults of this build):
+// Step-control constants of the forward integration (library defaults):
 // the Newton iteration stops when eta * |dZ| <= FP_KAPPA * tolerance; factors
 // are reused while h / h_factor stays in [FP_HRAT_LO, FP_HRAT_HI] and are
 // refreshed after a step whose contraction rate exceeded FP_THETA_REFAC.
@@ -1578,7 +1578,7 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
         return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
     }
     // stages 3: as many CTAs per SM as registers and shared memory allow
-    // (one with the register budget of this build)
+    // (one at the kernel's register budget)
     const size_t sm = make_layout<3>(L_launch).total;
     int per_sm = 0;
     cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
