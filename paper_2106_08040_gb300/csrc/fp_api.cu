@@ -66,6 +66,7 @@ int fp_destroy(fp_ctx* ctx) {
     cudaFree(ctx->d_blk_mem);
     cudaFree(ctx->d_lam);
     cudaFree(ctx->d_colT);
+    cudaFree(ctx->d_coef4);
     cudaFree(ctx->d_wdiag);
     cudaFree(ctx->d_tw);
     fp_free_tables(&ctx->host);
@@ -105,14 +106,29 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
         if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = fail(FP_ECUDA, "fp_setup: cudaMemcpy");
     };
-    up((void**)&c->d_coef, c->host.coef, N * FP_NSLOT * sizeof(double));
-    up((void**)&c->d_src, c->host.src, N * FP_NSLOT * sizeof(int));
+    {
+        // slot-major device copies (see DevTab)
+        std::vector<double> cT(N * FP_NSLOT), c4(N * FP_NSLOT), c4T(N * FP_NSLOT);
+        std::vector<int> sT(N * FP_NSLOT);
+        fp_build_coef4(&c->host, mat->alpha, c4.data());
+        for (size_t i = 0; i < N; ++i)
+            for (int k = 0; k < FP_NSLOT; ++k) {
+                cT[k * N + i] = c->host.coef[i * FP_NSLOT + k];
+                sT[k * N + i] = c->host.src[i * FP_NSLOT + k];
+                c4T[k * N + i] = c4[i * FP_NSLOT + k];
+            }
+        up((void**)&c->d_coef, cT.data(), cT.size() * sizeof(double));
+        up((void**)&c->d_src, sT.data(), sT.size() * sizeof(int));
+        up((void**)&c->d_coef4, c4T.data(), c4T.size() * sizeof(double));
+    }
     up((void**)&c->d_lam, c->host.lam, N * sizeof(double));
     up((void**)&c->d_wdiag, c->host.wdiag, N * sizeof(double));
     {
-        std::vector<FpPair> colT(N * FP_NCT);
+        std::vector<FpPair> colT(N * FP_NCT), colTT(N * FP_NCT);
         if (fp_build_columns(&c->host, colT.data()) != FP_OK) { fp_destroy(c); return fail(FP_EINVAL, "fp_setup: columns"); }
-        up((void**)&c->d_colT, colT.data(), colT.size() * sizeof(FpPair));
+        for (size_t i = 0; i < N; ++i)
+            for (int q = 0; q < FP_NCT; ++q) colTT[q * N + i] = colT[i * FP_NCT + q];
+        up((void**)&c->d_colT, colTT.data(), colTT.size() * sizeof(FpPair));
     }
     std::vector<double> tw(2 * (size_t)drive->samples_per_period);
     const double twopi = 6.283185307179586476925286766559;
@@ -199,7 +215,7 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     if (n < 0) return fail(FP_EINVAL, "fp_solve_batch: n < 0");
     if (n == 0) return FP_OK;
     if (!d_inst || !d_status) return fail(FP_EINVAL, "fp_solve_batch: NULL instance or status buffer");
-    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT};
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT, ctx->d_coef4, ctx->host.N};
     size_t sm = fp_solver_smem_bytes(ctx->tol.stages, ctx->L_max);
     int max_sm = 0;
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -231,7 +247,7 @@ int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max, const doub
     const long long need = fp_grad_workspace_bytes(ctx, n);
     if ((long long)work_bytes < need)
         return fail(FP_EINVAL, "fp_grad: workspace %llu bytes < %lld needed", work_bytes, need);
-    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT};
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT, ctx->d_coef4, ctx->host.N};
     size_t sm = fp_adjoint_smem_bytes(ctx->tol.stages, ctx->L_max);
     int max_sm = 0;
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -404,7 +420,7 @@ extern "C" int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, in
     // cotangents), so what an earlier call left there needs no clearing
     int grid = n < ctx->num_sms ? n : ctx->num_sms;
     if ((unsigned long long)grid > fit) grid = (int)fit;
-    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT};
+    DevTab tab{ctx->d_coef, ctx->d_src, ctx->d_lam, ctx->d_wdiag, ctx->d_colT, ctx->d_coef4, ctx->host.N};
     rc = fp_launch_adjoint(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
                            k_max, h_channels, C, d_dJ_dphihat, ctx->d_tw, d_grad, d_status, d_stats, scratch,
                            ctx->tol.max_steps, grid, (cudaStream_t)stream);

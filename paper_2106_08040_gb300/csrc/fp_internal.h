@@ -122,11 +122,16 @@ struct FpPair { int row, slot; };
 // Device views of the tables (pointers into context-owned device memory).
 #include <stdint.h>
 struct DevTab {
-    const double* coef;
-    const int* src;
-    const double* lam;
-    const double* wdiag;
-    const FpPair* colT;              // [N][FP_NCT] column view (row, slot)
+    // slot-major ("transposed") device copies: entry (row i, slot k) at
+    // k * nrow + i, so a warp over consecutive rows reads consecutive words
+    const double* coef;              // [FP_NSLOT][nrow]
+    const int* src;                  // [FP_NSLOT][nrow]
+    const double* lam;               // [nrow]
+    const double* wdiag;             // [nrow]
+    const FpPair* colT;              // [FP_NCT][nrow] column view (row, slot)
+    const double* coef4;             // [FP_NSLOT][nrow] coef with the G slots times alpha and the W slots
+                                     // times alpha/2: A(t) x in four scalar groups (anisotropy, x', y', z')
+    int nrow;                        // rows of the tables: (L_max + 1)^2
 };
 struct DevBlk {                      // block structure of every degree, packed
     const int* glob;
@@ -148,6 +153,7 @@ struct DevBlk {                      // block structure of every degree, packed
 // (row, slot) pairs with table[row][slot] having source i; row = -1 pads.
 #define FP_NCT 24
 int fp_build_columns(const FpTablesHost* t, FpPair* out);   // out: [N][FP_NCT]
+void fp_build_coef4(const FpTablesHost* t, double alpha, double* out);   // out: [N][FP_NSLOT]
 void fp_free_blocks(FpBlkHost* b);
 void fp_gauss_legendre(int n, double* x, double* w);
 
@@ -178,6 +184,7 @@ struct fp_ctx {
     double* d_lam;
     double* d_wdiag;
     FpPair* d_colT;           // column view of the tables (adjoint)
+    double* d_coef4;          // coefficients regrouped by field component (forward apply)
     DevBlk blk;               // device block structure, all degrees 2..L_max
     void* d_blk_mem;          // one allocation backing blk
     double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)

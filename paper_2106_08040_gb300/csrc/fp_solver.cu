@@ -53,7 +53,14 @@ __host__ __device__ constexpr int grp_of(int k) {
     return k < 2 ? 0 : k < 4 ? 1 : k < 5 ? 2 : k < 7 ? 3 : k < 9 ? 4 : k < 11 ? 5 : k < 15 ? 6 : 7;
 }
 
-struct AScal { double s[8]; };
+// slot -> group of the forward apply: anisotropy, x', y', z' (coef4 table)
+__host__ __device__ constexpr int grp4_of(int k) {
+    return k < 4 ? 0 : k == 4 ? 3 : k < 7 ? 1 : k < 9 ? 2 : k < 11 ? 3 : k < 15 ? 1 : 2;
+}
+
+// operator scalars: s per slot group (factorisation, adjoint) and s4 per
+// forward-apply group (-p3, -p1 B'_x, -p1 B'_y, -p1 B'_z)
+struct AScal { double s[8]; double s4[4]; };
 
 // ---------------------------------------------------------------- layout ----
 __host__ __device__ inline int nblk(int mu, int L) { return mu == 0 ? L + 1 : 2 * (L + 1 - mu); }
@@ -193,26 +200,32 @@ __device__ __forceinline__ AScal make_scal(const FpParams& P, const double* B) {
     s.s[5] = -P.p2 * B[2];
     s.s[6] = -P.p2 * B[0];
     s.s[7] = -P.p2 * B[1];
+    s.s4[0] = -P.p3;
+    s.s4[1] = -P.p1 * B[0];
+    s.s4[2] = -P.p1 * B[1];
+    s.s4[3] = -P.p1 * B[2];
     return s;
 }
 
-// row i of A x (FP64, matrix-free from the closed-form tables)
+// row i of A x (FP64, matrix-free from the closed-form tables, slots grouped
+// by the four forward-apply scalars)
 __device__ __forceinline__ double apply_row(int i, const double* __restrict__ x, const AScal& sc,
                                             const double* __restrict__ diag, int N, const DevTab& T) {
-    const double* cf = T.coef + (size_t)i * FP_NSLOT;
-    const int* sr = T.src + (size_t)i * FP_NSLOT;
-    double g[8];
+    const double* cf = T.coef4 + i;
+    const int* sr = T.src + i;
+    const int ld = T.nrow;
+    double g[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) g[q] = 0.0;
+    for (int q = 0; q < 4; ++q) g[q] = 0.0;
 #pragma unroll
     for (int k = 0; k < FP_NSLOT; ++k) {
-        int j = __ldg(sr + k);
+        int j = __ldg(sr + k * ld);
         double v = ((unsigned)j < (unsigned)N) ? x[j] : 0.0;
-        g[grp_of(k)] = fma(__ldg(cf + k), v, g[grp_of(k)]);
+        g[grp4_of(k)] = fma(__ldg(cf + k * ld), v, g[grp4_of(k)]);
     }
     double acc = diag[i] * x[i];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc = fma(sc.s[q], g[q], acc);
+    for (int q = 0; q < 4; ++q) acc = fma(sc.s4[q], g[q], acc);
     return acc;
 }
 
@@ -750,13 +763,25 @@ __device__ NewtonResult newton_stages(Ctx<S>& C, const DevTab& T, double hs, dou
 template <int S>
 __device__ void stage_scalars(const KArgs& A, const FpParams& P, const double* R, const double* off, double t,
                               double hs, bool pred, double h_old, Shared<S>& sh) {
+    const int lane = threadIdx.x & 31;
     if ((threadIdx.x >> 5) == 0) {
-        const int lane = threadIdx.x & 31;
+        // one drive component per lane (lane = 3 j + k), then lane j rotates
+        // stage j's field into the easy-axis frame
+        const double twopi = 6.283185307179586476925286766559;
+        double bk = 0.0;
+        if (lane < 3 * S) {
+            const int j = lane / 3, k = lane - 3 * j;
+            bk = off[k] + A.drv.amp[k] * sin(twopi * A.drv.freq[k] * (t + RAD<S>().c[j] * hs) + A.drv.phase[k]);
+        }
+        double bl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) bl[k] = __shfl_sync(FULLMASK, bk, (3 * lane + k) & 31);
         if (lane < S) {
             double Bj[3];
-            field_nframe(A, R, off, t + RAD<S>().c[lane] * hs, Bj);
+            for (int r = 0; r < 3; ++r) Bj[r] = R[3 * r] * bl[0] + R[3 * r + 1] * bl[1] + R[3 * r + 2] * bl[2];
             sh.scj[lane] = make_scal(P, Bj);
         }
+    } else if ((threadIdx.x >> 5) == 1) {
         if (pred && lane < S * S) {
             const int i = lane / S, j = lane - i * S;
             const double tau_i = 1.0 + RAD<S>().c[i] * (hs / h_old);
@@ -790,6 +815,13 @@ __device__ void predict_stages(Ctx<S>& C, bool pred, Shared<S>& sh) {
         for (int i = threadIdx.x; i < S * N; i += NT) C.Z[i] = 0.0;
     }
     __syncthreads();
+}
+
+// factorise the iteration matrices for step hs with the operator scalars sc of
+// its end point (stage S of the step, c_S = 1)
+template <int S>
+__device__ void refactor_at(Ctx<S>& C, const AScal& sc, double hs, Shared<S>& sh) {
+    factorize<S>(C, sc, hs, sh.pp, sh.colbuf);
 }
 
 // factorise the iteration matrices for step hs ending at t + hs
@@ -845,13 +877,11 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         apply_A(C.y, C.f0, sc0, C.diag, N, T);                 // f0 = A(t) y
         __syncthreads();
     }
-    auto write_sample = [&](int j, double tj) {
+    auto write_sample = [&](int j, const AScal& ss) {
         if (REC) return;
-        // <m> and d<m>/dt at t_j (l = 1 rows of A(t_j) y), rotated back to the lab frame
+        // <m> and d<m>/dt at t_j (l = 1 rows of A(t_j) y, ss = operator scalars
+        // at t_j), rotated back to the lab frame
         if (threadIdx.x < 3) {
-            double Bs[3];
-            field_nframe(A, R, off, tj, Bs);
-            AScal ss = make_scal(P, Bs);
             int row = threadIdx.x == 0 ? 3 : threadIdx.x;   // x' <- (1,1), y' <- (1,-1), z' <- (1,0)
             sh.dm[threadIdx.x] = sq43 * apply_row(row, C.y, ss, C.diag, N, T);
         }
@@ -874,7 +904,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         if (sh.dm[3] > (1.0 + 1e-6) * (1.0 + 1e-6) && out.status == FP_STATUS_OK) out.status = FP_STATUS_UNRESOLVED;
     };
 
-    if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, 0.0); jn = 1; }
+    if (sample_time(A.drv, 0) <= 0.0) { write_sample(0, make_scal(P, B)); jn = 1; }
 
     float ym = 0.f;
     for (int i = threadIdx.x; i < N; i += NT) ym = nanmax(ym, fabsf((float)C.y[i]));
@@ -894,16 +924,17 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         const double nrem = ceil(rem / fmin(h, T_s) * (1.0 - 1e-12));
         const bool last = nrem <= 1.0;
         const double hs = last ? rem : rem / nrem;
+        stage_scalars<S>(A, P, R, off, t, hs, have_pred, h_old, sh);
+        const AScal s_end = sh.scj[S - 1];           // operator scalars at t + hs (c_S = 1)
         const double rat = fac_valid ? hs / h_f : 0.0;
         if (!fac_valid || force_refac || rat < FP_HRAT_LO || rat > FP_HRAT_HI || since_fac >= A.tol.refactor_every) {
-            refactor<S>(C, A, P, R, off, t, hs, sh);
+            refactor_at<S>(C, s_end, hs, sh);
             h_f = hs; t_f = t; fac_valid = true; force_refac = false; since_fac = 0; ++out.nfac;
         }
         if (REC && out.nsteps % FP_CKPT == 0) {       // checkpoint the state before this step
             double* ck = rec_ckpt + (size_t)(out.nsteps / FP_CKPT) * N;
             for (int i = threadIdx.x; i < N; i += NT) ck[i] = C.y[i];
         }
-        stage_scalars<S>(A, P, R, off, t, hs, have_pred, h_old, sh);
         predict_stages<S>(C, have_pred, sh);
         const double sc_err = atol + rtol * ymax;
         const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_err, eta, FP_KAPPA, A.tol.newton_max_iter, sh);
@@ -950,18 +981,10 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
             if (!(ymax <= 3.0e38)) { out.status = FP_STATUS_NONFINITE; break; }
             ++out.nsteps; ++since_fac;
             t = last ? tt : t + hs;
-            {   // f0 = A(t) y at the accepted point, for the next error estimate
-                if (threadIdx.x == 0) {
-                    double Bn[3];
-                    field_nframe(A, R, off, t, Bn);
-                    sh.scj[0] = make_scal(P, Bn);
-                }
-                __syncthreads();
-                const AScal sn = sh.scj[0];
-                apply_A(C.y, C.f0, sn, C.diag, N, T);
-                __syncthreads();
-            }
-            if (last) { write_sample(jn, tt); ++jn; }
+            // f0 = A(t) y at the accepted point, for the next error estimate
+            apply_A(C.y, C.f0, s_end, C.diag, N, T);
+            __syncthreads();
+            if (last) { write_sample(jn, s_end); ++jn; }
             double hn = hs * fmin(4.0, fmax(0.2, fac));
             if (last && hs < h) hn = fac < 1.0 ? fmin(h, hn) : h;
             // keep the factorised step when the controller asks for a small change
@@ -1046,9 +1069,9 @@ __device__ __forceinline__ double apply_row_T(int i, const double* __restrict__ 
     double acc = diag[i] * x[i];
 #pragma unroll 4
     for (int q = 0; q < FP_NCT; ++q) {
-        const FpPair pr = T.colT[(size_t)i * FP_NCT + q];
+        const FpPair pr = T.colT[(size_t)q * T.nrow + i];
         if ((unsigned)pr.row >= (unsigned)N) continue;
-        acc = fma(sc.s[grp_of(pr.slot)] * __ldg(T.coef + (size_t)pr.row * FP_NSLOT + pr.slot), x[pr.row], acc);
+        acc = fma(sc.s[grp_of(pr.slot)] * __ldg(T.coef + (size_t)pr.slot * T.nrow + pr.row), x[pr.row], acc);
     }
     return acc;
 }
@@ -1112,13 +1135,13 @@ __device__ void bilinear(const double* xi, const double* yv, int N, const DevTab
     for (int q = 0; q < 10; ++q) beta[q] = 0.0;
     for (int i = threadIdx.x; i < N; i += NT) {
         const double xv = xi[i];
-        const double* cf = T.coef + (size_t)i * FP_NSLOT;
-        const int* sr = T.src + (size_t)i * FP_NSLOT;
+        const double* cf = T.coef + i;
+        const int* sr = T.src + i;
 #pragma unroll
         for (int k = 0; k < FP_NSLOT; ++k) {
-            int j = __ldg(sr + k);
+            int j = __ldg(sr + (size_t)k * T.nrow);
             double v = ((unsigned)j < (unsigned)N) ? yv[j] : 0.0;
-            beta[grp_of(k)] = fma(xv * __ldg(cf + k), v, beta[grp_of(k)]);
+            beta[grp_of(k)] = fma(xv * __ldg(cf + (size_t)k * T.nrow), v, beta[grp_of(k)]);
         }
         beta[8] = fma(xv * __ldg(T.lam + i), yv[i], beta[8]);
         beta[9] = fma(xv * __ldg(T.wdiag + i), yv[i], beta[9]);
@@ -1155,9 +1178,9 @@ __device__ void readout_adjoint(Ctx<S>& C, const KArgs& A, const FpParams& P, co
             const double e = sq43 * vp[q];
             C.lam[r] = fma(C.diag[r], e, C.lam[r]);
             for (int k = 0; k < FP_NSLOT; ++k) {
-                int j = __ldg(T.src + (size_t)r * FP_NSLOT + k);
+                int j = __ldg(T.src + (size_t)k * T.nrow + r);
                 if ((unsigned)j >= (unsigned)N) continue;
-                C.lam[j] = fma(sc.s[grp_of(k)] * __ldg(T.coef + (size_t)r * FP_NSLOT + k), e, C.lam[j]);
+                C.lam[j] = fma(sc.s[grp_of(k)] * __ldg(T.coef + (size_t)k * T.nrow + r), e, C.lam[j]);
             }
         }
         // direct parameter terms: g . dR^T/dp m'dot + sqrt(4pi/3) vp . ((dA/dp) c)_rows
@@ -1174,9 +1197,9 @@ __device__ void readout_adjoint(Ctx<S>& C, const KArgs& A, const FpParams& P, co
                 const int r = rows[q];
                 double dr = ds[p].dl * __ldg(T.lam + r) * cst[r] + ds[p].dw * __ldg(T.wdiag + r) * cst[r];
                 for (int k = 0; k < FP_NSLOT; ++k) {
-                    int j = __ldg(T.src + (size_t)r * FP_NSLOT + k);
+                    int j = __ldg(T.src + (size_t)k * T.nrow + r);
                     if ((unsigned)j >= (unsigned)N) continue;
-                    dr = fma(ds[p].s[grp_of(k)] * __ldg(T.coef + (size_t)r * FP_NSLOT + k), cst[j], dr);
+                    dr = fma(ds[p].s[grp_of(k)] * __ldg(T.coef + (size_t)k * T.nrow + r), cst[j], dr);
                 }
                 acc = fma(sq43 * vp[q], dr, acc);
             }

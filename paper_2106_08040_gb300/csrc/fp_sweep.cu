@@ -64,7 +64,7 @@ int launch_bucket(fp_sweep* sw, int bi, const fp_instance* d_inst, double* d_m, 
     fp_tol tol = c->tol;
     tol.stages = bk.stages;
     tol.refactor_every = bk.refactor_every;
-    DevTab tab{c->d_coef, c->d_src, c->d_lam, c->d_wdiag, c->d_colT};
+    DevTab tab{c->d_coef, c->d_src, c->d_lam, c->d_wdiag, c->d_colT, c->d_coef4, c->host.N};
     const size_t sm = fp_solver_smem_bytes(bk.stages, bk.L);
     int max_sm = 0;
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);

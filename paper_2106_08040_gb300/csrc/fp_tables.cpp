@@ -395,6 +395,19 @@ int fp_build_columns(const FpTablesHost* t, FpPair* out) {
     return FP_OK;
 }
 
+// The forward apply groups the slots by the scalar that multiplies them:
+// -(p4/2) W - p3 M_zR_z = -p3 (M_zR_z + (alpha/2) W) and, per easy-axis-frame
+// field component k, -p1 B_k R_k - p2 B_k G_k = -p1 B_k (R_k + alpha G_k)
+// (p4 = alpha p3, p2 = alpha p1, Sec. 2.1), so the W and G coefficients are
+// stored pre-multiplied by alpha/2 and alpha.
+void fp_build_coef4(const FpTablesHost* t, double alpha, double* out) {
+    for (int r = 0; r < t->N; ++r)
+        for (int k = 0; k < FP_NSLOT; ++k) {
+            const double f = k < SL_ZR ? 0.5 * alpha : k >= SL_GZ ? alpha : 1.0;
+            out[r * FP_NSLOT + k] = f * t->coef[r * FP_NSLOT + k];
+        }
+}
+
 void fp_free_blocks(FpBlkHost* b) {
     std::free(b->glob); std::free(b->sb_k); std::free(b->sb_g); std::free(b->sb_cf);
     std::free(b->dn_k); std::free(b->dn_g); std::free(b->dn_cf);
