@@ -145,10 +145,23 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
     return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 __device__ __forceinline__ float2 cfma(float a, float2 b, float2 c) { return make_float2(fmaf(a, b.x, c.x), fmaf(a, b.y, c.y)); }
-__device__ __forceinline__ float crecip(float a) { return 1.f / a; }
+__device__ __forceinline__ float crecip(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ float2 crecip(float2 a) {
-    float d = 1.f / (a.x * a.x + a.y * a.y);
+    float d = __frcp_rn(a.x * a.x + a.y * a.y);
     return make_float2(a.x * d, -a.y * d);
+}
+// a[idx] for a register array of power-of-two length M (log2 M select levels)
+template <class T, int M>
+__device__ __forceinline__ T tree_pick(const T* a, int idx) {
+    T t[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) t[i] = a[i];
+#pragma unroll
+    for (int w = M / 2; w >= 1; w /= 2) {
+#pragma unroll
+        for (int i = 0; i < w; ++i) t[i] = (idx & w) ? t[i + w] : t[i];
+    }
+    return t[0];
 }
 __device__ __forceinline__ float cneg(float a) { return -a; }
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
@@ -317,9 +330,7 @@ __device__ void group_factor_block(Ctx<S>& C, int mu, T shift, const float* gs, 
         const int owner = k / CPW, kk = k - owner * CPW;
         T* cb = colbuf + (k & 1) * 32;
         if (gw == owner) {
-            T ak = a[0];
-#pragma unroll
-            for (int jj = 1; jj < CPW; ++jj) ak = jj == kk ? a[jj] : ak;
+            const T ak = tree_pick<T, CPW>(a, kk);
             const float v = used ? 0.f : cabs1(ak);
             unsigned key = (__float_as_uint(v) & ~31u) | (unsigned)lane;
             key = __reduce_max_sync(FULLMASK, key);
