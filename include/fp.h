@@ -326,6 +326,49 @@ int fp_surrogate_grad(const fp_surrogate_train* t, const float* d_x, const float
 int fp_surrogate_adam(const fp_surrogate_train* t, float* const* d_gW, float* const* d_gb, float lr, float beta1,
                       float beta2, float eps, int step, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Data-driven system-matrix models (Sec. 2.2) and distance measures (Sec. 2.3).
+ * System matrices are laid out like fp_signal's output, [voxel][channel][k]
+ * complex (re, im), k = 0..K1-1.
+ * ------------------------------------------------------------------------- */
+
+/* Model M0 (Sec. 2.2, Eq. Langevin): the equilibrium mean moment
+ *     <m>_equ(t) = L(bT |B|) B / |B|,  L(x) = coth x - 1/x,  bT = V Ms / (kB T),
+ * V = pi d^3 / 6, B(t) = h_off + drive (the context's drive, schedule and
+ * material; K, theta, phi are ignored), and its exact time derivative, at the
+ * output samples of fp_solve_batch and in its layouts d_m, d_dmdt [n][S][3]
+ * (either may be NULL, not both).  fp_signal on d_dmdt gives M0's phi_hat_D.
+ * Instances with d <= 0 or flags != 0 get zero outputs. */
+int fp_equilibrium(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, double* d_dmdt, void* stream);
+
+/* Model M1 (and M0) fit of Sec. 2.2 ("Technical details"), for Q dictionary
+ * elements Phi_q against one measured system matrix S:
+ *     a_q[c][k] = S_k conj(Phi_q,k)^T / ||Phi_q,k||_2^2        (row k, channel c)
+ *     eps_q[c][k] = (1/sqrt(N)) ||S_k - a_q[c][k] Phi_q,k||_2 / ||S_k||_inf   (Eq. error1)
+ * d_phi [Q][N][C][K1][2], d_S [N][C][K1][2]; outputs d_a [Q][C][K1][2],
+ * d_eps [Q][C][K1], d_smax [C][K1] (= ||S_k||_inf).  A row with Phi = 0 gets
+ * a = 0; a row with S = 0 gets eps = 0.  Q <= 65535.  Two passes over the data. */
+int fp_m1_fit(const double* d_phi, int Q, const double* d_S, int N, int C, int K1, double* d_a, double* d_eps,
+              double* d_smax, void* stream);
+
+/* Distance measures of Sec. 2.3 from row errors d_eps [A][C][K1] (A angles,
+ * C receive channels): per frequency eps_freq[k] = sqrt(mean_{angle, c}
+ * eps^2) into d_eps_freq [K1] (may be NULL), and the global measure
+ * (eq. globalMeasure) sqrt(mean_{k in I_freq} eps_freq[k]^2) into
+ * *d_eps_global, with the nk rows d_ks (device ints, each < K1). */
+int fp_nrmse(const double* d_eps, int A, int C, int K1, const int* d_ks, int nk, double* d_eps_freq,
+             double* d_eps_global, void* stream);
+
+/* Host only.  Mixing orders of frequency index k (Eq. mix):
+ * k = m_x n_dens + m_y (n_dens + 1) with the smallest |m_x| + |m_y|; ties go
+ * to the smaller |m_x|, then to m_x >= 0. */
+int fp_mixing_order(int k, int n_dens, int* mx, int* my);
+
+/* Host only.  I_freq of Sec. 2.3: the distinct k(m_x, m_y) <= k_limit for
+ * 0 <= m_x <= M_x, 0 <= m_y <= M_y without the orders (0,0), (0,1), (1,0), in
+ * increasing order; the first cap of them into h_ks, their number into *count. */
+int fp_freq_index_set(int M_x, int M_y, int n_dens, int k_limit, int* h_ks, int cap, int* count);
+
 /* Diagnostic (host only, no GPU needed): dense Galerkin matrix A of
  * dc/dt = A c (Eq. FP-general tested against the real SH basis) for one
  * instance in the EASY-AXIS frame (n = z), with the field B_nframe [T] already

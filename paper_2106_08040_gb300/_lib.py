@@ -17,7 +17,8 @@ EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_sol
             "fp_signal", "fp_grad_workspace_bytes", "fp_grad", "fp_grad_noalloc", "fp_surrogate_workspace_bytes", "fp_surrogate_infer",
             "fp_surrogate_grad", "fp_surrogate_adam", "fp_sweep_plan", "fp_sweep_order", "fp_sweep_run",
             "fp_sweep_autotune", "fp_sweep_info", "fp_sweep_destroy", "fp_operator_dense", "fp_peak_fp64",
-            "fp_status_str", "fp_last_error"]
+            "fp_status_str", "fp_last_error", "fp_equilibrium", "fp_m1_fit", "fp_nrmse", "fp_mixing_order",
+            "fp_freq_index_set"]
 
 
 class fp_material(C.Structure):
@@ -114,6 +115,16 @@ def lib():
     L.fp_sweep_info.restype = i
     L.fp_sweep_destroy.argtypes = [vp]
     L.fp_sweep_destroy.restype = i
+    L.fp_equilibrium.argtypes = [vp, vp, i, vp, vp, vp]
+    L.fp_equilibrium.restype = i
+    L.fp_m1_fit.argtypes = [vp, i, vp, i, i, i, vp, vp, vp, vp]
+    L.fp_m1_fit.restype = i
+    L.fp_nrmse.argtypes = [vp, i, i, i, vp, i, vp, vp, vp]
+    L.fp_nrmse.restype = i
+    L.fp_mixing_order.argtypes = [i, i, C.POINTER(i), C.POINTER(i)]
+    L.fp_mixing_order.restype = i
+    L.fp_freq_index_set.argtypes = [i, i, i, i, C.POINTER(i), i, C.POINTER(i)]
+    L.fp_freq_index_set.restype = i
     L.fp_peak_fp64.argtypes = [C.POINTER(d)]
     L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]

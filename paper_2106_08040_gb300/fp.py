@@ -155,6 +155,44 @@ def fp_signal(ctx: Context, d_dmdt, n: int, k_max: int, channels, d_phihat, stre
                                _stream_ptr(stream)), "fp_signal")
 
 
+def fp_equilibrium(ctx: Context, d_inst, n: int, d_m=None, d_dmdt=None, stream=None):
+    """Model M0 traces (Sec. 2.2, Eq. Langevin) in the layouts of fp_solve_batch."""
+    check(_lib.lib().fp_equilibrium(ctx.handle, _ptr(d_inst), int(n), _ptr(d_m), _ptr(d_dmdt), _stream_ptr(stream)),
+          "fp_equilibrium")
+
+
+def fp_m1_fit(d_phi, Q: int, d_S, N: int, C: int, K1: int, d_a, d_eps, d_smax, stream=None):
+    """Model M1 fit per dictionary element, channel and row (Sec. 2.2) and the
+    row errors of Eq. error1."""
+    check(_lib.lib().fp_m1_fit(_ptr(d_phi), int(Q), _ptr(d_S), int(N), int(C), int(K1), _ptr(d_a), _ptr(d_eps),
+                               _ptr(d_smax), _stream_ptr(stream)), "fp_m1_fit")
+
+
+def fp_nrmse(d_eps, A: int, C: int, K1: int, d_ks, nk: int, d_eps_freq, d_eps_global, stream=None):
+    """Per-frequency and global NRMSE (Sec. 2.3)."""
+    check(_lib.lib().fp_nrmse(_ptr(d_eps), int(A), int(C), int(K1), _ptr(d_ks), int(nk), _ptr(d_eps_freq),
+                              _ptr(d_eps_global), _stream_ptr(stream)), "fp_nrmse")
+
+
+def fp_mixing_order(k: int, n_dens: int):
+    """(m_x, m_y) of frequency index k (Eq. mix)."""
+    mx, my = C.c_int(), C.c_int()
+    check(_lib.lib().fp_mixing_order(int(k), int(n_dens), C.byref(mx), C.byref(my)), "fp_mixing_order")
+    return mx.value, my.value
+
+
+def fp_freq_index_set(M_x: int, M_y: int, n_dens: int, k_limit: int):
+    """I_freq of Sec. 2.3 as a numpy int32 array."""
+    cnt = C.c_int()
+    check(_lib.lib().fp_freq_index_set(int(M_x), int(M_y), int(n_dens), int(k_limit), None, 0, C.byref(cnt)),
+          "fp_freq_index_set")
+    out = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    check(_lib.lib().fp_freq_index_set(int(M_x), int(M_y), int(n_dens), int(k_limit),
+                                       out.ctypes.data_as(C.POINTER(C.c_int)), int(out.size), C.byref(cnt)),
+          "fp_freq_index_set")
+    return out[:cnt.value]
+
+
 def fp_grad_workspace_bytes(ctx: Context, n: int) -> int:
     v = _lib.lib().fp_grad_workspace_bytes(ctx.handle, int(n))
     if v < 0:
