@@ -33,7 +33,6 @@ sys.path.insert(0, ROOT)
 METRIC = "FP instance-periods/s at ≤1e-9 rel err vs FP64 oracle; surrogate speedup at 1e-3"
 UNIT = "instance-periods/s"
 L2_FLUSH_BYTES = 256 << 20
-SOLVER_S5_TRAFFIC_BYTES = (2.51 + 94.30) * 1e6   # dram read + write of one fp_solve_kernel<5> launch, full workload
 
 
 def parse():
@@ -52,6 +51,7 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the uneven-sweep measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    p.add_argument("--no-models", action="store_true", help="skip the M0/M1 model measurement")
     p.add_argument("--sweep-instances", type=int, default=2048)
     return p.parse_args()
 
@@ -164,19 +164,18 @@ def operator_nnz(fp, L):
 
 # -------------------------------------------------------------- CPU oracle ----
 def _oracle_window(args):
-    """One bounded oracle solve: voxel k of the workload, first `ns` samples."""
+    """One bounded oracle solve: voxel rec of the workload, ns samples starting at
+    output sample j0.  Setup (weak-form matrices) and the start state (Boltzmann
+    density at the window's start field) are not timed."""
     import os as _os
     _os.environ.setdefault("OMP_NUM_THREADS", "1")
-    (dspec_d, rec, ns, rtol) = args
-    from oracle import physics, solve
+    (dspec_d, rec, j0, ns, rtol) = args
+    from oracle import galerkin, physics, radau, solve
     drive = physics.Drive(amp=dspec_d["amp"], freq=dspec_d["freq"], phase=dspec_d["phase"], period=dspec_d["period"])
-    sched = solve.Schedule(dspec_d["samples_per_period"], 0, 1)
     inst = solve.Instance(h_off=tuple(rec["h_off"]), theta=float(rec["theta"]), phi=float(rec["phi"]),
                           K=float(rec["K"]), d=float(rec["d"]), L=int(rec["L"]))
     P = physics.derive(physics.Material(), inst.K, inst.d)
-    from oracle import galerkin, radau
     n = physics.easy_axis(inst.theta, inst.phi)
-    t0 = time.time()
     A0, A1 = galerkin.weak_form_matrices(inst.L, P, n)
     off = np.asarray(inst.h_off)
 
@@ -184,47 +183,54 @@ def _oracle_window(args):
         B = drive.field(t, off)
         return A0 + B[0] * A1[0] + B[1] * A1[1] + B[2] * A1[2]
 
-    c0 = galerkin.boltzmann_coeffs(inst.L, P, n, drive.field(0.0, off))
-    T_s = drive.period / sched.samples_per_period
-    t_out = (np.arange(ns) + 1) * T_s
+    S = dspec_d["samples_per_period"]
+    T_s = drive.period / S
+    t_start = (dspec_d["warmup_periods"] + j0 / S) * drive.period
+    c_start = galerkin.boltzmann_coeffs(inst.L, P, n, drive.field(t_start, off))
+    t_out = t_start + (np.arange(ns) + 1) * T_s
     integ = radau.RadauIIA(A_of_t, rtol=rtol, h0=min(T_s, 0.01 * P.tau), h_max=T_s)
-    integ.integrate(0.0, c0, t_out)
-    return time.time() - t0, ns / dspec_d["samples_per_period"], integ.n_steps
+    t0 = time.time()
+    integ.integrate(t_start, c_start, t_out)
+    return time.time() - t0, ns / S, integ.n_steps
 
 
-def cpu_oracle_sample(dspec, inst, target_s, rtol=1e-10):
-    """Oracle on all host cores (spawned single-threaded processes), each over the
-    first samples of one voxel's period; throughput scaled to instance-periods/s."""
+def cpu_oracle_sample(dspec, inst, target_s, rtol=1e-12):
+    """Oracle (its defining tolerance, rtol 1e-12) on all host cores, one
+    single-threaded process per core, each timing a window of output samples of
+    one voxel; the windows start at evenly spread positions of the output period,
+    so together they cover its field sweep.  Throughput is extrapolated linearly
+    by sample count to instance-periods/s (one instance-period = S samples)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
-    dd = dict(amp=dspec.amp, freq=dspec.freq, phase=dspec.phase, period=dspec.period,
-              samples_per_period=dspec.samples_per_period)
-    # calibrate the window on one process: 4 samples
+    S = dspec.samples_per_period
+    dd = dict(amp=dspec.amp, freq=dspec.freq, phase=dspec.phase, period=dspec.period, samples_per_period=S,
+              warmup_periods=dspec.warmup_periods)
     rng = np.random.default_rng(0)
-    picks = rng.choice(len(inst), size=cores, replace=False)
-    el, frac, _ = _oracle_window((dd, inst[picks[0]], 4, rtol))
-    per_sample = max(el / 4, 1e-3)
-    ns = int(max(4, min(dspec.samples_per_period, target_s / per_sample)))
+    picks = rng.choice(len(inst), size=cores, replace=cores > len(inst))
+    starts = [(q * S) // cores for q in range(cores)]
+    el, _, _ = _oracle_window((dd, inst[picks[0]], starts[0], 2, rtol))      # calibration: 2 samples
+    per_sample = max(el / 2, 1e-3)
+    ns = int(max(2, min(S // cores, target_s / per_sample)))
     ctx = mp.get_context("spawn")
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"                         # children: single-threaded BLAS, one per core
     try:
-        t0 = time.time()
         with ctx.Pool(cores) as pool:
-            res = pool.map(_oracle_window, [(dd, inst[k], ns, rtol) for k in picks])
-        wall = time.time() - t0
+            res = pool.map(_oracle_window, [(dd, inst[k], j0, ns, rtol) for k, j0 in zip(picks, starts)])
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    ip = sum(r[1] for r in res)
-    return {"value": ip / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d voxels of the 32x32 L=16 batch, first %d of 1632 samples of the first period each "
-                      "(Radau IIA rtol 1e-10, one process per core); %.3f instance-periods in %.1f s wall"
-                      % (cores, ns, ip, wall)}
+    # each process solves its own window: the job rate is the sum of the per-process rates
+    rate = sum(r[1] / r[0] for r in res)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": "%d voxels of the 32x32 L=16 batch, one window of %d output samples each, windows at %d evenly "
+                      "spread positions of the output period (Radau IIA rtol 1e-12, one process per core; setup and "
+                      "the window's start state untimed); %d oracle steps in %.1f s of CPU; instance-periods/s "
+                      "extrapolated by sample count" % (cores, ns, cores, sum(r[2] for r in res), sum(r[0] for r in res))}
 
 
 # --------------------------------------------------------------- surrogate --
@@ -340,13 +346,98 @@ def adjoint_leg(fp, dev, n_inst=152):
     torch.cuda.synchronize()
     t_f, t_a = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     periods = dspec.warmup_periods + dspec.output_periods
+    # gradient error: central differences (relative step 1e-4) of the 5-stage
+    # forward at rtol 1e-11 on the first two voxels
+    g = grad.cpu().numpy()
+    Gh = dJ.cpu().numpy()
+    ctx5 = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-11, stages=5), 16)
+    recs, steps = [], []
+    for i in (0, 1):
+        for p, key in enumerate(["K", "d", "theta", "phi"]):
+            for sgn in (1, -1):
+                r = inst[i:i + 1].copy()
+                h = 1e-4 * abs(float(r[key][0])) if p < 2 else 1e-4
+                r[key] = r[key] + sgn * h
+                recs.append(r)
+                steps.append(h)
+    allr = np.concatenate(recs)
+    _, dmf, stf, _ = fp.solve(ctx5, allr, want_m=False)
+    phf = torch.empty((len(allr), 2, K + 1, 2), dtype=torch.float64, device=dev)
+    fp.fp_signal(ctx5, dmf, len(allr), K, ch, phf)
+    torch.cuda.synchronize()
+    phf = phf.cpu().numpy()
+    rel_err = []
+    for a, i in enumerate((0, 1)):
+        fd = np.array([((phf[a * 8 + 2 * p] - phf[a * 8 + 2 * p + 1]) * Gh[i]).sum() / (2 * steps[a * 8 + 2 * p])
+                       for p in range(4)])
+        w = np.array([inst[i]["K"], inst[i]["d"], 1.0, 1.0])
+        rel_err.append((np.abs((g[i] - fd) * w) / np.linalg.norm(fd * w)).tolist())
+    ctx5.close()
     out = {"instances": n, "forward_ms": t_f, "adjoint_ms": t_a, "adjoint_over_forward": t_a / t_f,
            "gradients_per_s": n / (t_a * 1e-3), "instance_periods_per_s": n * periods / (t_a * 1e-3),
            "status_ok": int((st.cpu().numpy() == 0).sum()), "workspace_bytes": int(work.numel()),
            "failed_phase_counts": np.bincount(gstats[:, 2].cpu().numpy(), minlength=4).tolist(),
+           "grad_rel_err_vs_central_differences": {"voxels": [0, 1], "per_parameter": rel_err,
+                                                   "max": float(np.max(rel_err)),
+                                                   "reference": "central differences, relative step 1e-4, of "
+                                                                "fp_solve_batch + fp_signal at rtol 1e-11 (5 stages); "
+                                                                "error in units of the gradient norm"},
            "workload": "first %d voxels of the 32x32 system-matrix batch, L = 16, Radau s = 3, rtol 1e-9, "
                        "checkpoints every 64 steps" % n}
     ctx.close()
+    return out
+
+
+def models_leg(fp, dev, Q=96):
+    """Sec. 2.2 models on the system-matrix grid: M0 traces + phi_hat for the
+    1024 voxels, and the M1 fit of a Q-element dictionary (8 diameters x 12
+    anisotropies at one angle, synthetic phi_hat of the solver's shape) against
+    one measured matrix.  fp_m1_fit reads the dictionary twice (filter, then
+    row errors): HBM-bound."""
+    import torch
+    from paper_2106_08040_gb300 import workloads
+    dspec, inst = workloads.system_matrix_workload()
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(), 8)
+    n, S, K1, C = len(inst), ctx.num_samples(), 817, 2
+    d_inst = fp.instances_to_device(inst, dev)
+    dm = torch.empty((n, S, 3), dtype=torch.float64, device=dev)
+    ph = torch.empty((n, C, K1, 2), dtype=torch.float64, device=dev)
+    ch = [[1.0, 0, 0], [0, 1.0, 0]]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(2):
+        fp.fp_equilibrium(ctx, d_inst, n, None, dm)
+        fp.fp_signal(ctx, dm, n, K1 - 1, ch, ph)
+    e[0].record()
+    fp.fp_equilibrium(ctx, d_inst, n, None, dm)
+    fp.fp_signal(ctx, dm, n, K1 - 1, ch, ph)
+    e[1].record()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1)
+    phi = torch.randn((Q, n, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
+    Sm = torch.randn((n, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
+    a = torch.empty((Q, C, K1, 2), dtype=torch.float64, device=dev)
+    eps = torch.empty((Q, C, K1), dtype=torch.float64, device=dev)
+    smax = torch.empty((C, K1), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        fp.fp_m1_fit(phi, Q, Sm, n, C, K1, a, eps, smax)
+    torch.cuda.synchronize()
+    reps = 5
+    e[2].record()
+    for _ in range(reps):
+        fp.fp_m1_fit(phi, Q, Sm, n, C, K1, a, eps, smax)
+    e[3].record()
+    torch.cuda.synchronize()
+    ms_m0 = e[0].elapsed_time(e[1])
+    ms_m1 = e[2].elapsed_time(e[3]) / reps
+    by = 2.0 * (phi.numel() + Sm.numel()) * 8 + (a.numel() + eps.numel()) * 8
+    peak, src = measured_peak("hbm_gbs", 6800.0)
+    out = {"m0_voxels": n, "m0_ms": ms_m0, "m0_voxel_periods_per_s": n * 2 / (ms_m0 * 1e-3),
+           "m1_dictionary": Q, "m1_ms": ms_m1, "m1_fits_per_s": Q / (ms_m1 * 1e-3),
+           "m1_roofline": {"bound": "hbm", "achieved": by / (ms_m1 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": by / (ms_m1 * 1e-3) / 1e9 / peak, "peak_source": src,
+                           "bytes_per_launch": by, "kernel": "fp_m1_pass1 + fp_m1_pass2"}}
+    ctx.close()
+    del phi
     return out
 
 
@@ -471,13 +562,9 @@ def run_gpu(args):
     # roofline of the dominant kernel (the solver): FP64 pipe
     flops = float(fp64_flops_per_instance(sts, (L + 1) ** 2, nnz, args.stages).sum())
     achieved = flops / (t_solve * 1e-3) / 1e12
-    # DRAM bytes per launch from the one-pass ncu capture of this kernel on this workload
-    # (profiles/solver_s5_system_matrix_L16.md); null for any other configuration
-    full = n == 1024 and periods == 2 and L == 16
-    traffic = SOLVER_S5_TRAFFIC_BYTES if (full and args.stages == 5 and args.rtol == 1e-9 and world == 1) else None
+    # DRAM traffic is not measured inside the run (it needs a profiler): null
     roof = {"bound": "alu", "achieved": achieved, "peak": peak / 1e3, "unit": "TFLOP/s",
-            "frac": achieved / (peak / 1e3), "traffic": traffic,
-            "traffic_source": "profiles/solver_s5_system_matrix_L16.md" if traffic else None,
+            "frac": achieved / (peak / 1e3), "traffic": None,
             "kernel": "fp_solve_kernel<%d> (FP64 pipe)" % args.stages,
             "peak_source": "measured FP64 FMA throughput (fp_peak_fp64, this GPU, this run)"}
     # end-to-end through the public API: host instances -> solve -> phi_hat -> host
@@ -531,6 +618,8 @@ def run_gpu(args):
             out["sweep"] = sweep_leg(fp, dev, args.sweep_instances)
         if not args.no_adjoint:
             out["adjoint"] = adjoint_leg(fp, dev)
+        if not args.no_models:
+            out["models"] = models_leg(fp, dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

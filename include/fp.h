@@ -188,6 +188,15 @@ int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_widt
  * FP_EINVAL. */
 int fp_sweep_order(const fp_material* mat, const fp_drive* drv, int L_max, const fp_instance* h_inst, int n,
                    int bucket_width, int* h_order, int* h_bucket_L, int* h_bucket_count, int* n_buckets);
+/* Host only.  Truncation degree per instance (a reading of the paper, which
+ * fixes no degree): L = clamp(L_min, L_max, ceil(2 + 5.5 sqrt(sigma + xi_max))),
+ * sigma = K V / (kB T), xi_max = bT (|h_off| + |drive amplitude|), V = pi d^3 / 6,
+ * bT = V Ms / (kB T).  The coefficients fit the degree at which the
+ * spherical-harmonic tail of the Boltzmann density beyond L - 2 falls below
+ * 1e-8 of its mean (sigma in [0.5, 12], xi in [0, 20]).  h_L[n] receives the
+ * degrees; sweeps plan with the same rule. */
+int fp_truncation_degree(const fp_material* mat, const fp_drive* drv, const fp_instance* h_inst, int n, int L_min,
+                         int L_max, int* h_L);
 int fp_sweep_run(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_dmdt, int* d_status,
                  int* d_stats, void* stream);
 int fp_sweep_autotune(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_dmdt, int* d_status,

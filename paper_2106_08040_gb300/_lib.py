@@ -18,7 +18,7 @@ EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_sol
             "fp_surrogate_grad", "fp_surrogate_adam", "fp_sweep_plan", "fp_sweep_order", "fp_sweep_run",
             "fp_sweep_autotune", "fp_sweep_info", "fp_sweep_destroy", "fp_operator_dense", "fp_peak_fp64",
             "fp_status_str", "fp_last_error", "fp_equilibrium", "fp_m1_fit", "fp_nrmse", "fp_mixing_order",
-            "fp_freq_index_set"]
+            "fp_freq_index_set", "fp_truncation_degree"]
 
 
 class fp_material(C.Structure):
@@ -125,6 +125,8 @@ def lib():
     L.fp_mixing_order.restype = i
     L.fp_freq_index_set.argtypes = [i, i, i, i, C.POINTER(i), i, C.POINTER(i)]
     L.fp_freq_index_set.restype = i
+    L.fp_truncation_degree.argtypes = [C.POINTER(fp_material), C.POINTER(fp_drive), vp, i, i, i, C.POINTER(i)]
+    L.fp_truncation_degree.restype = i
     L.fp_peak_fp64.argtypes = [C.POINTER(d)]
     L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]

@@ -100,6 +100,25 @@ int enqueue_all(fp_sweep* sw, const fp_instance* d_inst, double* d_m, double* d_
 
 }  // namespace
 
+extern "C" int fp_truncation_degree(const fp_material* mat, const fp_drive* drv, const fp_instance* h_inst, int n,
+                                    int L_min, int L_max, int* h_L) {
+    if (!mat || !drv || (n > 0 && (!h_inst || !h_L)) || n < 0 || L_min < 2 || L_max < L_min)
+        return fp_fail(FP_EINVAL, "fp_truncation_degree: bad argument");
+    const double kT = FP_KB * mat->T_B;
+    const double amp = std::sqrt(drv->amp[0] * drv->amp[0] + drv->amp[1] * drv->amp[1] + drv->amp[2] * drv->amp[2]);
+    for (int i = 0; i < n; ++i) {
+        const fp_instance& in = h_inst[i];
+        const double V = 3.14159265358979323846 * in.d * in.d * in.d / 6.0;
+        const double hb = std::sqrt(in.h_off[0] * in.h_off[0] + in.h_off[1] * in.h_off[1] + in.h_off[2] * in.h_off[2]);
+        const double x = in.K * V / kT + V * mat->Ms / kT * (hb + amp);
+        double Lr = std::ceil(2.0 + 5.5 * std::sqrt(x > 0.0 ? x : 0.0));
+        if (!(Lr >= L_min)) Lr = L_min;          // also for a NaN
+        if (Lr > L_max) Lr = L_max;
+        h_L[i] = (int)Lr;
+    }
+    return FP_OK;
+}
+
 extern "C" {
 
 int fp_sweep_order(const fp_material* mat, const fp_drive* drv, int L_max, const fp_instance* h_inst, int n,

@@ -330,19 +330,19 @@ def solve(ctx: Context, inst: np.ndarray, want_m=True, want_dmdt=True, stream=No
 
 
 def truncation_degree(inst, material=None, drive=None, L_min=8, L_max=16):
-    """Per-instance truncation degree L = clamp(L_min, L_max, ceil(2 + 5.5 sqrt(sigma + xi_max))),
-    sigma = K V/(k_B T), xi_max = b_T (|B_off| + |B_drive amplitude|).  The
-    coefficients (2, 5.5) fit the degree at which the Boltzmann density's
-    spherical-harmonic tail beyond L - 2 falls below 1e-8 of its mean
-    (equilibrium projections over sigma in [0.5, 12], xi in [0, 20])."""
+    """Per-instance truncation degree (fp_truncation_degree of the C ABI):
+    L = clamp(L_min, L_max, ceil(2 + 5.5 sqrt(sigma + xi_max)))."""
     material = material or Material()
-    V = np.pi * np.asarray(inst["d"]) ** 3 / 6.0
-    kT = 1.380649e-23 * material.T_B
-    sigma = np.asarray(inst["K"]) * V / kT
-    amp = 0.0 if drive is None else float(np.linalg.norm(drive.amp))
-    xi = V * material.Ms / kT * (np.linalg.norm(np.asarray(inst["h_off"]), axis=1) + amp)
-    L = np.ceil(2.0 + 5.5 * np.sqrt(sigma + xi)).astype(int)
-    return np.clip(L, L_min, L_max)
+    if drive is None:
+        drive = Drive(amp=(0.0, 0.0, 0.0), freq=(0.0, 0.0, 0.0), phase=(0.0, 0.0, 0.0), period=1.0,
+                      samples_per_period=2, warmup_periods=0, output_periods=1)
+    rec = np.ascontiguousarray(np.asarray(inst).astype(INSTANCE_DTYPE))
+    out = np.zeros(max(len(rec), 1), dtype=np.int32)
+    mat, drv = material.c(), drive.c()
+    check(_lib.lib().fp_truncation_degree(C.byref(mat), C.byref(drv), rec.ctypes.data_as(C.c_void_p), len(rec),
+                                          int(L_min), int(L_max), out.ctypes.data_as(C.POINTER(C.c_int))),
+          "fp_truncation_degree")
+    return out[:len(rec)].astype(int)
 
 
 def sweep_order(inst: np.ndarray, material: Material, drive: Drive, L_max: int, bucket_width=1):
