@@ -388,7 +388,7 @@ def adjoint_leg(fp, dev, n_inst=152):
     return out
 
 
-def models_leg(fp, dev, Q=96):
+def models_leg(fp, dev, peak64, Q=96):
     """Sec. 2.2 models on the system-matrix grid: M0 traces + phi_hat for the
     1024 voxels, and the M1 fit of a Q-element dictionary (8 diameters x 12
     anisotropies at one angle, synthetic phi_hat of the solver's shape) against
@@ -437,7 +437,38 @@ def models_leg(fp, dev, Q=96):
                            "frac": by / (ms_m1 * 1e-3) / 1e9 / peak, "peak_source": src,
                            "bytes_per_launch": by, "kernel": "fp_m1_pass1 + fp_m1_pass2"}}
     ctx.close()
-    del phi
+    del phi, Sm
+    # M2 at the paper's shapes: 12 angles, an 11 x 11 voxel grid, J = 8 x 12
+    # (D, K) tuples, both channels, rows I_freq (mixing orders up to 20)
+    A2, J2, N2 = 12, 96, 121
+    ks = fp.fp_freq_index_set(20, 20, 16, K1 - 1)
+    phi2 = torch.randn((A2, J2, N2, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
+    a2 = torch.randn((A2, J2, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
+    S2 = torch.randn((A2, N2, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
+    smax2 = torch.sqrt((S2 ** 2).sum(-1)).amax(1).contiguous()
+    d_ks = torch.from_numpy(ks.astype(np.int32)).to(dev)
+    G = torch.empty((J2 + 1, J2 + 1, 2), dtype=torch.float64, device=dev)
+    fp.fp_m2_gram(phi2, a2, S2, smax2, A2, J2, N2, C, K1, d_ks, len(ks), G)
+    torch.cuda.synchronize()
+    e[0].record()
+    fp.fp_m2_gram(phi2, a2, S2, smax2, A2, J2, N2, C, K1, d_ks, len(ks), G)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms_g = e[0].elapsed_time(e[1])
+    t0 = time.time()
+    w, obj, res, sv, srank = fp.fp_m2_solve(G.cpu().numpy(), J2, 21)
+    t_host = time.time() - t0
+    rows = A2 * N2 * C * len(ks)
+    tiles = -(-(J2 + 1) // 16)
+    flops = 8.0 * rows * (16 * 16) * tiles * (tiles + 1) / 2      # complex multiply-adds of the computed tiles
+    flops_alg = 8.0 * rows * (J2 + 1) * (J2 + 2) / 2              # upper triangle of the Gram matrix
+    out.update({"m2_gram_ms": ms_g, "m2_rows": rows, "m2_J": J2, "m2_angles": A2, "m2_voxels": N2,
+                "m2_host_solve_s": t_host, "m2_rank": srank, "m2_nonzero_weights": int((w > 1e-12 * w.max()).sum()),
+                "m2_gram_roofline": {"bound": "alu", "achieved": flops_alg / (ms_g * 1e-3) / 1e12, "peak": peak64,
+                                     "unit": "TFLOP/s", "frac": flops_alg / (ms_g * 1e-3) / 1e12 / peak64,
+                                     "executed_over_algorithmic": flops / flops_alg,
+                                     "kernel": "fp_m2_gram_kernel (FP64, upper-triangle tiles)"}})
+    del phi2, a2, S2
     return out
 
 
@@ -619,7 +650,7 @@ def run_gpu(args):
         if not args.no_adjoint:
             out["adjoint"] = adjoint_leg(fp, dev)
         if not args.no_models:
-            out["models"] = models_leg(fp, dev)
+            out["models"] = models_leg(fp, dev, peak / 1e3)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

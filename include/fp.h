@@ -368,6 +368,39 @@ int fp_m1_fit(const double* d_phi, int Q, const double* d_S, int N, int C, int K
 int fp_nrmse(const double* d_eps, int A, int C, int K1, const int* d_ks, int nk, double* d_eps_freq,
              double* d_eps_global, void* stream);
 
+/* Model M2, second step (Sec. 2.2, eq. LSfitM2 / eq. LSfitM2_alternative).
+ * Dictionary Psi_{theta,j} = diag(a_{theta,j}) Phi_{theta,j} for A angles and
+ * J parameter tuples (D, K); rows r = (angle, voxel, channel, k in ks), each
+ * weighted by Sigma = 1 / ||S_{theta,k}||_inf per channel (d_smax [A][C][K1]
+ * as fp_m1_fit returns it per angle; a zero entry drops the row).  With the
+ * columns M[r][j] = Sigma Psi_{theta,j} and y[r] = Sigma S_theta, fp_m2_gram
+ * writes the complex Gram matrix of [M | y] into d_G [(J+1)][(J+1)][2]:
+ *     G[i][j] = sum_r conj(M[r][i]) M[r][j]   (column J is y)
+ * for i <= j (the Hermitian upper triangle; entries below it are left
+ * unspecified).  d_phi [A][J][N][C][K1][2], d_a [A][J][C][K1][2],
+ * d_S [A][N][C][K1][2], d_ks [nk] rows (device ints < K1).  FP64, summed by
+ * row blocks with atomic adds (the summation order varies between calls);
+ * d_G is cleared on the stream first; fp_m2_gram_bytes(J) gives its size. */
+long long fp_m2_gram_bytes(int J);
+int fp_m2_gram(const double* d_phi, const double* d_a, const double* d_S, const double* d_smax, int A, int J, int N,
+               int C, int K1, const int* d_ks, int nk, double* d_G, void* stream);
+
+/* Host only.  Non-negative M2 weights from the Gram matrix h_G of fp_m2_gram
+ * (host copy; its upper triangle is read).  M^H M = V diag(s^2) V^H gives the truncated problem of
+ * eq. approx_low_rank, min_{w >= 0} ||U_s^H (M w - y)||_2^2 with
+ * U_s^H M = diag(s_1..s_s) V_s^H and U_s^H y = diag(1/s) V_s^H M^H y, its
+ * complex rows split into real and imaginary parts; s = s_rank (<= 0: all
+ * numerically nonzero singular values).  The quadratic program
+ * min 1/2 w^T Q w + f^T w, w >= 0 is solved by a primal-dual interior-point
+ * method.  Outputs: h_w [J], *h_objective = the truncated objective,
+ * *h_residual = ||M w - y||_2^2, h_sv [J] = singular values of M (each of
+ * the three may be NULL).  Returns the rank s used (>= 0), or a negative
+ * FP_E* code (FP_EUNSUPPORTED if the iteration does not converge).  The
+ * eigen-decomposition is a cyclic Jacobi method on a 2J x 2J real matrix:
+ * O(J^3) per sweep. */
+int fp_m2_solve(const double* h_G, int J, int s_rank, double* h_w, double* h_objective, double* h_residual,
+                double* h_sv);
+
 /* Host only.  Mixing orders of frequency index k (Eq. mix):
  * k = m_x n_dens + m_y (n_dens + 1) with the smallest |m_x| + |m_y|; ties go
  * to the smaller |m_x|, then to m_x >= 0. */

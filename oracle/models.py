@@ -155,16 +155,12 @@ def eps_global(eps_by_angle, ks):
 
 
 # ------------------------------------------------------------------ M2 -----
-def m2_weights(Psi, S, ks, s_rank=None):
-    """Model M2 weights.  Psi: [angles][J] dictionary system matrices
-    psi = diag(a_q) phi_q, each [N, C, K]; S: [angles] measured matrices
-    [N, C, K]; ks: rows used (I_freq).  Sigma_theta = diag(1/||S_theta,k||_inf)
-    per channel and row; M stacks the columns vec(Sigma Psi_q) over the angles
-    (eq. LSfitM2_alternative), y = vec(Sigma S).  With s_rank the problem is
-    projected on the first s left singular vectors of M (eq. approx_low_rank).
-    Complex residuals with real weights are split into real and imaginary
-    parts; w >= 0 by non-negative least squares.  Returns (w, ||M w - y||_2,
-    singular values of M)."""
+def m2_matrix(Psi, S, ks):
+    """The Sigma-weighted dictionary matrix M and data y of eq. LSfitM2_alternative.
+    Psi: [angles][J] dictionary system matrices psi = diag(a_q) phi_q, each
+    [N, C, K]; S: [angles] measured matrices [N, C, K]; ks: rows used (I_freq).
+    Sigma_theta = diag(1/||S_theta,k||_inf) per channel and row; M stacks the
+    columns vec(Sigma Psi_q) over the angles, y = vec(Sigma S)."""
     ks = np.asarray(ks)
     cols, ys = [], []
     for Pa, Sa in zip(Psi, S):
@@ -172,8 +168,17 @@ def m2_weights(Psi, S, ks, s_rank=None):
         sig = 1.0 / np.max(np.abs(Sk), axis=0)                 # [C, K]
         ys.append((sig[None] * Sk).reshape(-1))
         cols.append(np.stack([(sig[None] * np.asarray(p)[:, :, ks]).reshape(-1) for p in Pa], axis=1))
-    M = np.concatenate(cols, axis=0)
-    y = np.concatenate(ys)
+    return np.concatenate(cols, axis=0), np.concatenate(ys)
+
+
+def m2_weights(Psi, S, ks, s_rank=None):
+    """Model M2 weights for the matrix M and data y of ``m2_matrix``.  With
+    s_rank the problem is projected on the first s left singular vectors of M
+    (eq. approx_low_rank).  Complex residuals with real weights are split into
+    real and imaginary parts; w >= 0 by non-negative least squares.  Returns
+    (w, ||M w - y||_2, singular values of M, the minimised objective
+    ||G w - h||_2^2 of the (projected) problem)."""
+    M, y = m2_matrix(Psi, S, ks)
     U, sv, Vh = np.linalg.svd(M, full_matrices=False)
     if s_rank is None:
         G, h = M, y
@@ -183,4 +188,4 @@ def m2_weights(Psi, S, ks, s_rank=None):
     Gr = np.concatenate([G.real, G.imag], axis=0)
     hr = np.concatenate([h.real, h.imag])
     w, _ = nnls(Gr, hr, maxiter=50 * Gr.shape[1])
-    return w, float(np.linalg.norm(M @ w - y)), sv
+    return w, float(np.linalg.norm(M @ w - y)), sv, float(np.linalg.norm(Gr @ w - hr) ** 2)

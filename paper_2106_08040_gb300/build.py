@@ -12,7 +12,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfp.so")
-SOURCES = ["fp_api.cu", "fp_solver.cu", "fp_tables.cpp", "fp_radau.cpp", "fp_peak.cu", "fp_mlp.cu", "fp_sweep.cu", "fp_models.cu"]
+SOURCES = ["fp_api.cu", "fp_solver.cu", "fp_tables.cpp", "fp_radau.cpp", "fp_peak.cu", "fp_mlp.cu", "fp_sweep.cu", "fp_models.cu", "fp_m2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

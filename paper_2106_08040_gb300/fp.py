@@ -193,6 +193,27 @@ def fp_freq_index_set(M_x: int, M_y: int, n_dens: int, k_limit: int):
     return out[:cnt.value]
 
 
+def fp_m2_gram(d_phi, d_a, d_S, d_smax, A: int, J: int, N: int, C_: int, K1: int, d_ks, nk: int, d_G, stream=None):
+    """Complex Gram matrix of the Sigma-weighted M2 dictionary augmented with the data (Sec. 2.2)."""
+    check(_lib.lib().fp_m2_gram(_ptr(d_phi), _ptr(d_a), _ptr(d_S), _ptr(d_smax), int(A), int(J), int(N), int(C_),
+                                int(K1), _ptr(d_ks), int(nk), _ptr(d_G), _stream_ptr(stream)), "fp_m2_gram")
+
+
+def fp_m2_solve(G, J: int, s_rank: int = 0):
+    """M2 weights w >= 0 from a host Gram matrix [(J+1),(J+1),2]: (w, truncated
+    objective, ||M w - y||^2, singular values, rank used)."""
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    w = np.zeros(J)
+    sv = np.zeros(J)
+    obj, res = C.c_double(), C.c_double()
+    dp = C.POINTER(C.c_double)
+    rc = _lib.lib().fp_m2_solve(G.ctypes.data_as(dp), int(J), int(s_rank), w.ctypes.data_as(dp), C.byref(obj),
+                                C.byref(res), sv.ctypes.data_as(dp))
+    if rc < 0:
+        check(rc, "fp_m2_solve")
+    return w, obj.value, res.value, sv, rc
+
+
 def fp_grad_workspace_bytes(ctx: Context, n: int) -> int:
     v = _lib.lib().fp_grad_workspace_bytes(ctx.handle, int(n))
     if v < 0:

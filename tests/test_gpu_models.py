@@ -127,3 +127,38 @@ def test_empty_inputs_are_noops(fp):
     z = torch.zeros(2, dtype=torch.float64, device="cuda")
     fp.fp_m1_fit(z, 0, z, 4, 1, 1, z, z, z)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("A,J,N,C,K1,nk", [(3, 6, 40, 2, 12, 11), (2, 37, 29, 2, 50, 23)])
+def test_m2_gram_and_weights_match_oracle(fp, A, J, N, C, K1, nk):
+    """fp_m2_gram against the oracle's explicit Sigma-weighted matrix [M | y]
+    (sums of R = A N C nk products: bar 1e-12 relative to the largest entry),
+    tiles with a ragged edge (J + 1 not a multiple of 16), a row subset ks;
+    then the host M2 solve from the GPU Gram matrix against the oracle's
+    weights (full rank: the minimiser is unique)."""
+    from oracle import models
+    rng = np.random.default_rng(A * 100 + J)
+    Phi = _cplx(rng, (A, J, N, C, K1))
+    a = _cplx(rng, (A, J, C, K1))
+    w_true = np.abs(rng.normal(size=J)) * (rng.uniform(size=J) < 0.5)
+    Psi = [[a[t, j][None] * Phi[t, j] for j in range(J)] for t in range(A)]
+    S = [sum(w_true[j] * Psi[t][j] for j in range(J)) + 0.05 * _cplx(rng, (N, C, K1)) for t in range(A)]
+    ks = np.sort(rng.choice(K1, size=nk, replace=False)).astype(np.int32)
+    smax = np.stack([np.abs(St).max(0) for St in S])
+    G = torch.empty((J + 1, J + 1, 2), dtype=torch.float64, device="cuda")
+    fp.fp_m2_gram(_dev(Phi), _dev(a), _dev(np.stack(S)), torch.from_numpy(smax).cuda(), A, J, N, C, K1,
+                  torch.from_numpy(ks).cuda(), nk, G)
+    torch.cuda.synchronize()
+    Gg = G.cpu().numpy()
+    Gg = Gg[..., 0] + 1j * Gg[..., 1]
+    M, y = models.m2_matrix(Psi, S, ks)
+    My = np.concatenate([M, y[:, None]], axis=1)
+    Go = np.conj(My.T) @ My
+    iu = np.triu_indices(J + 1)
+    assert np.abs(Gg[iu] - Go[iu]).max() <= 1e-12 * np.abs(Go).max()
+    Gfull = np.triu(Gg) + np.conj(np.triu(Gg, 1).T)
+    w, obj, res, sv, s = fp.fp_m2_solve(np.stack([Gfull.real, Gfull.imag], -1), J)
+    wo, reso, svo, objo = models.m2_weights(Psi, S, ks)
+    assert s == J
+    np.testing.assert_allclose(w, wo, atol=1e-7 * np.abs(wo).max())
+    assert abs(np.sqrt(res) - reso) <= 1e-8 * reso

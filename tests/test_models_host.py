@@ -26,3 +26,52 @@ def test_freq_index_set_matches_oracle(fp):
         ref = models.freq_index_set(mx, my, 16)
         ref = ref[ref <= 816]
         np.testing.assert_array_equal(fp.fp_freq_index_set(mx, my, 16, 816), ref)
+
+
+def _rand_complex(rng, shape):
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def _gram(M, y):
+    My = np.concatenate([M, y[:, None]], axis=1)
+    G = np.conj(My.T) @ My
+    return np.ascontiguousarray(np.stack([G.real, G.imag], -1))
+
+
+def test_m2_solve_recovers_planted_weights(fp):
+    """Host M2 solve (fp_m2_solve) from an exact Gram matrix: a planted
+    non-negative superposition is recovered with zero residual."""
+    rng = np.random.default_rng(5)
+    Psi = [[_rand_complex(rng, (40, 2, 12)) for _ in range(6)] for _ in range(3)]
+    w_true = np.array([0.0, 1.5, 0.0, 0.25, 2.0, 0.0])
+    S = [sum(w * p for w, p in zip(w_true, Pa)) for Pa in Psi]
+    ks = np.arange(1, 12)
+    M, y = models.m2_matrix(Psi, S, ks)
+    w, obj, res, sv, s = fp.fp_m2_solve(_gram(M, y), 6)
+    assert s == 6
+    np.testing.assert_allclose(w, w_true, atol=1e-8)
+    assert res <= 1e-12 * np.vdot(y, y).real
+    np.testing.assert_allclose(sv, np.linalg.svd(M, compute_uv=False), rtol=1e-10)
+
+
+@pytest.mark.parametrize("s_rank", [0, 4])
+def test_m2_solve_matches_oracle(fp, s_rank):
+    """Noisy data: full rank (unique minimiser: the weights agree) and a
+    truncated SVD of rank 4 < J = 6 (the minimiser is not unique; the
+    truncated objective, which is, agrees, and the weights are feasible)."""
+    rng = np.random.default_rng(6)
+    Psi = [[_rand_complex(rng, (40, 2, 12)) for _ in range(6)] for _ in range(3)]
+    S = [sum(w * p for w, p in zip([1.0, 0.5, 0.0, 2.0, 0.1, 0.0], Pa)) + 0.3 * _rand_complex(rng, (40, 2, 12))
+         for Pa in Psi]
+    ks = np.arange(12)
+    M, y = models.m2_matrix(Psi, S, ks)
+    w, obj, res, sv, s = fp.fp_m2_solve(_gram(M, y), 6, s_rank)
+    wo, reso, svo, objo = models.m2_weights(Psi, S, ks, s_rank=s_rank or None)
+    assert (w >= 0).all()
+    if s_rank == 0:
+        np.testing.assert_allclose(w, wo, atol=1e-7 * np.abs(wo).max())
+        assert abs(np.sqrt(res) - reso) <= 1e-9 * reso
+    else:
+        assert s == 4
+        assert abs(obj - objo) <= 1e-9 * objo
+        assert abs(np.sqrt(res) - np.linalg.norm(M @ w - y)) <= 1e-9 * np.linalg.norm(y)

@@ -130,10 +130,10 @@ def test_m2_recovers_planted_weights():
     w_true = np.array([0.0, 1.5, 0.0, 0.25, 2.0, 0.0])
     S = [sum(w * p for w, p in zip(w_true, Pa)) for Pa in Psi]
     ks = np.arange(1, 12)
-    w, res, sv = models.m2_weights(Psi, S, ks)
+    w, res, sv, _ = models.m2_weights(Psi, S, ks)
     np.testing.assert_allclose(w, w_true, atol=1e-10)
     assert res <= 1e-10
-    w6, res6, _ = models.m2_weights(Psi, S, ks, s_rank=6)
+    w6, res6, _, _ = models.m2_weights(Psi, S, ks, s_rank=6)
     np.testing.assert_allclose(w6, w_true, atol=1e-9)
 
 
@@ -145,13 +145,16 @@ def test_m2_solution_satisfies_the_kkt_conditions():
     Psi = _m2_dictionary(rng)
     S = [_rand_complex(rng, Psi[0][0].shape) for _ in Psi]
     ks = np.arange(12)
-    w, res, sv = models.m2_weights(Psi, S, ks)
+    w, res, sv, _ = models.m2_weights(Psi, S, ks)
     cols, ys = [], []
     for Pa, Sa in zip(Psi, S):
         sig = 1.0 / np.abs(Sa).max(0)
         ys.append((sig * Sa).reshape(-1))
         cols.append(np.stack([(sig * p).reshape(-1) for p in Pa], 1))
     M, y = np.concatenate(cols), np.concatenate(ys)
+    M2, y2 = models.m2_matrix(Psi, S, ks)
+    np.testing.assert_array_equal(M, M2)
+    np.testing.assert_array_equal(y, y2)
     A = np.real(np.conj(M.T) @ M)
     f = -np.real(np.conj(M.T) @ y)
     g = A @ w + f
