@@ -276,7 +276,8 @@ int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
  * (fp_solve_batch + fp_signal) produces its training data and is the reference for its error.
  * Layers l = 0..4: z_l = W_l x_l + b_l with x_0 the normalised, zero-padded
  * input (64 wide), x_{l+1} = gelu(z_l) (exact erf form) for l < 4 and the
- * output y = z_4 * out_scale + out_shift.  BF16 operands, FP32 accumulation on
+ * output y = z_4 * out_scale + out_shift; gelu(x) = x (1 + erf(x / sqrt 2)) / 2
+ * with erf evaluated by Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7).  BF16 operands, FP32 accumulation on
  * the tensor cores (tcgen05, TMEM accumulators, TMA-fed shared memory).
  * Weight layouts (row-major, bf16): W_l [N_l][K_l] with K = (64, 512, 512,
  * 512, 512), N = (512, 512, 512, 512, 800); columns 7..63 of W_0 must be 0.
@@ -308,8 +309,9 @@ typedef struct {
     float* vb[FP_SUR_LAYERS];
 } fp_surrogate_train;
 
-/* Device workspace (bytes) for q queries: inference (training = 0) or one
- * gradient evaluation (training = 1; q must then be a multiple of 8). */
+/* Device workspace (bytes) for q queries: inference (training = 0), one
+ * gradient evaluation (training = 1; q must then be a multiple of 8), or
+ * ensemble inference (training = 2, fp_surrogate_infer_ensemble). */
 long long fp_surrogate_workspace_bytes(int q, int training);
 
 /* Surrogate inference: d_x [q][7] f32 -> d_y [q][800] f32.  d_err (device
@@ -319,6 +321,17 @@ long long fp_surrogate_workspace_bytes(int q, int training);
  * Asynchronous. */
 int fp_surrogate_infer(const fp_surrogate* net, const float* d_x, int q, float* d_y, void* d_work,
                        unsigned long long work_bytes, int* d_err, void* stream);
+
+/* Two-network ensemble (the paper has no surrogate; its fallback and error
+ * judge is the solver): d_mean [q][800] = (y_0 + y_1) / 2 and d_spread [q] =
+ * ||y_0 - y_1||_2 / (2 ||mean||_2), the members' disagreement used to send a
+ * query to the solver.  The second network's last GEMM folds its output into
+ * the mean in its epilogue and accumulates both norms per query there.
+ * Workspace fp_surrogate_workspace_bytes(q, 2); otherwise as
+ * fp_surrogate_infer. */
+int fp_surrogate_infer_ensemble(const fp_surrogate* net0, const fp_surrogate* net1, const float* d_x, int q,
+                                float* d_mean, float* d_spread, void* d_work, unsigned long long work_bytes,
+                                int* d_err, void* stream);
 
 /* Loss and gradients of one batch: loss = sum over queries and outputs of
  * (z_4 - (y - out_shift)/out_scale)^2, written to *d_loss (f32, overwritten);

@@ -18,7 +18,7 @@ EXPORTED = ["fp_max_degree", "fp_setup", "fp_destroy", "fp_num_samples", "fp_sol
             "fp_surrogate_grad", "fp_surrogate_adam", "fp_sweep_plan", "fp_sweep_order", "fp_sweep_run",
             "fp_sweep_autotune", "fp_sweep_info", "fp_sweep_destroy", "fp_operator_dense", "fp_peak_fp64",
             "fp_status_str", "fp_last_error", "fp_equilibrium", "fp_m1_fit", "fp_nrmse", "fp_mixing_order",
-            "fp_freq_index_set", "fp_truncation_degree", "fp_m2_gram_bytes", "fp_m2_gram", "fp_m2_solve"]
+            "fp_freq_index_set", "fp_truncation_degree", "fp_m2_gram_bytes", "fp_m2_gram", "fp_m2_solve", "fp_surrogate_infer_ensemble"]
 
 
 class fp_material(C.Structure):
@@ -133,6 +133,9 @@ def lib():
     L.fp_m2_gram.restype = i
     L.fp_m2_solve.argtypes = [C.POINTER(d), i, i, C.POINTER(d), C.POINTER(d), C.POINTER(d), C.POINTER(d)]
     L.fp_m2_solve.restype = i
+    L.fp_surrogate_infer_ensemble.argtypes = [C.POINTER(fp_surrogate), C.POINTER(fp_surrogate), vp, i, vp, vp, vp,
+                                              C.c_ulonglong, vp, vp]
+    L.fp_surrogate_infer_ensemble.restype = i
     L.fp_peak_fp64.argtypes = [C.POINTER(d)]
     L.fp_peak_fp64.restype = i
     L.fp_status_str.argtypes = [i]

@@ -41,6 +41,8 @@ enum Epi : int {
     EPI_OUT_TRAIN = 3,      // g = gscale (acc + b - (y - oshift)/oscale); loss += (.)^2; out, outT = bf16(g)
     EPI_DX_GELU = 4,        // g = acc * gelu'(zin); out, outT = bf16(g)
     EPI_DW = 5,             // outf = acc (f32)
+    EPI_OUT_ENSEMBLE = 6,   // y1 = (acc + b) * oscale + oshift; outf holds y0 and receives (y0 + y1) / 2;
+                            // rowacc[row] += (|y0 - y1|^2, |mean|^2)
 };
 
 struct EpiParams {
@@ -54,6 +56,7 @@ struct EpiParams {
     const float* oshift;            // [N]
     const float* oscale;            // [N]
     float* loss;                    // scalar accumulator (EPI_OUT_TRAIN)
+    float* rowacc;                  // [M][2] per-row sums (EPI_OUT_ENSEMBLE)
     float gscale;
     int* err;
     int nk;                         // number of 64-wide K blocks
@@ -156,10 +159,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// erf by Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7, far below the BF16
+// resolution of the activations): erf(x) = 1 - t (a1 + t (a2 + ... a5 t)) exp(-x^2),
+// t = 1 / (1 + p x) for x >= 0, odd in x
+__device__ __forceinline__ float erf_as(float z) {
+    const float x = fabsf(z);
+    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.f));
+    float y = fmaf(1.061405429f, t, -1.453152027f);
+    y = fmaf(y, t, 1.421413741f);
+    y = fmaf(y, t, -0.284496736f);
+    y = fmaf(y, t, 0.254829592f);
+    const float e = 1.f - y * t * __expf(-x * x);
+    return copysignf(e, z);
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erf_as(x * 0.70710678118654752f)); }
 
 __device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+    return 0.5f * (1.f + erf_as(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
 
 template <int BN> struct Cfg {
@@ -181,8 +198,41 @@ constexpr int MAX_EPI_COLS = 1024;           // bias / output scale staged in sh
 // sb, ssc, ssh: bias, output scale and shift of this chunk's 16 columns (shared memory)
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk(const EpiParams& P, int row, int col0, float* v, const float* sb,
-                                               const float* ssc, const float* ssh) {
+                                               const float* ssc, const float* ssh, float* racc) {
     const bool rv = row < P.M;
+    if (EPI == EPI_OUT_ENSEMBLE) {
+        if (!rv) return;
+        float* o = P.outf + (size_t)row * P.ldf + col0;
+        float y0[16];
+        const bool full = col0 + 16 <= P.N && ((P.ldf & 3) == 0);
+        if (full) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) {
+                const float4 a = *(const float4*)(o + i);
+                y0[i] = a.x; y0[i + 1] = a.y; y0[i + 2] = a.z; y0[i + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y0[i] = col0 + i < P.N ? o[i] : 0.f;
+        }
+        float mn[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const bool cv = col0 + i < P.N;
+            const float y1 = (v[i] + sb[i]) * ssc[i] + ssh[i];
+            const float d = cv ? y0[i] - y1 : 0.f;
+            mn[i] = cv ? 0.5f * (y0[i] + y1) : 0.f;
+            racc[0] = fmaf(d, d, racc[0]);
+            racc[1] = fmaf(mn[i], mn[i], racc[1]);
+        }
+        if (full) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) *(float4*)(o + i) = make_float4(mn[i], mn[i + 1], mn[i + 2], mn[i + 3]);
+        } else {
+            for (int i = 0; i < 16 && col0 + i < P.N; ++i) o[i] = mn[i];
+        }
+        return;
+    }
     if (EPI == EPI_DW) {
         if (!rv) return;
         float* o = P.outf + (size_t)row * P.ldf + col0;
@@ -387,11 +437,17 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             tc_fence_after();
             const int row = m0 + lg * 32 + lane;
             const uint32_t tw = tmem + (uint32_t)(b * C::TMEM_COLS) + ((uint32_t)(lg * 32) << 16);
+            float racc[2] = {0.f, 0.f};
 #pragma unroll 1
             for (int c = c_lo; c < c_hi; c += 16) {
                 float v[16];
                 tmem_ld16(tw + c, v);
-                if (n0 + c < P.N) epilogue_chunk<EPI>(P, row, n0 + c, v, s_bias + n0 + c, s_osc + n0 + c, s_osh + n0 + c);
+                if (n0 + c < P.N)
+                    epilogue_chunk<EPI>(P, row, n0 + c, v, s_bias + n0 + c, s_osc + n0 + c, s_osh + n0 + c, racc);
+            }
+            if (EPI == EPI_OUT_ENSEMBLE && row < P.M) {
+                atomicAdd(P.rowacc + 2 * (size_t)row, racc[0]);
+                atomicAdd(P.rowacc + 2 * (size_t)row + 1, racc[1]);
             }
             tc_fence_before();
             __syncwarp();
@@ -491,6 +547,7 @@ int gemm(int epi, int BN, const void* A, int lda, const void* B, int ldb, int M,
         case EPI_OUT_TRAIN: return launch_bn<EPI_OUT_TRAIN>(BN, ma, mb, P, M, N, st);
         case EPI_DX_GELU: return launch_bn<EPI_DX_GELU>(BN, ma, mb, P, M, N, st);
         case EPI_DW: return launch_bn<EPI_DW>(BN, ma, mb, P, M, N, st);
+        case EPI_OUT_ENSEMBLE: return launch_bn<EPI_OUT_ENSEMBLE>(BN, ma, mb, P, M, N, st);
         default: return FP_EINVAL;
     }
 }
@@ -624,29 +681,22 @@ extern "C" {
 
 long long fp_surrogate_workspace_bytes(int q, int training) {
     if (q < 1) return fp_fail(FP_EINVAL, "fp_surrogate_workspace_bytes: q=%d", q);
+    if (training == 2) return (long long)(infer_ws(q, nullptr, nullptr) + al256((size_t)q * 2 * sizeof(float)));
     return (long long)(training ? train_ws(q, nullptr, nullptr) : infer_ws(q, nullptr, nullptr));
 }
 
-int fp_surrogate_infer(const fp_surrogate* net, const float* d_x, int q, float* d_y, void* d_work,
-                       unsigned long long work_bytes, int* d_err, void* stream) {
-    if (!net || !d_x || !d_y || !d_work) return fp_fail(FP_EINVAL, "fp_surrogate_infer: NULL argument");
-    if (q < 0) return fp_fail(FP_EINVAL, "fp_surrogate_infer: q=%d", q);
-    if (q == 0) return FP_OK;
+// one network's forward pass; the last layer's epilogue is EPI_OUT_INFER into
+// d_y, or EPI_OUT_ENSEMBLE folding this network's output into the mean in d_y
+static int infer_member(const fp_surrogate* net, const float* d_x, int q, float* d_y, const InferWs& w, int* d_err,
+                        float* rowacc, cudaStream_t st, const char* who) {
     for (int l = 0; l < FP_SUR_LAYERS; ++l)
-        if (!net->W[l] || !net->b[l]) return fp_fail(FP_EINVAL, "fp_surrogate_infer: layer %d not set", l);
+        if (!net->W[l] || !net->b[l]) return fp_fail(FP_EINVAL, "%s: layer %d not set", who, l);
     if (!net->in_shift || !net->in_scale || !net->out_shift || !net->out_scale)
-        return fp_fail(FP_EINVAL, "fp_surrogate_infer: normalisation not set");
-    if (work_bytes < infer_ws(q, nullptr, nullptr))
-        return fp_fail(FP_EINVAL, "fp_surrogate_infer: workspace %llu < %zu bytes", work_bytes,
-                       infer_ws(q, nullptr, nullptr));
-    if (!d_err) return fp_fail(FP_EINVAL, "fp_surrogate_infer: d_err is required");
-    cudaStream_t st = (cudaStream_t)stream;
-    InferWs w;
-    infer_ws(q, (unsigned char*)d_work, &w);
+        return fp_fail(FP_EINVAL, "%s: normalisation not set", who);
     const long long tot = (long long)q * FP_SUR_KIN;
     prep_input_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d_x, q, net->in_shift, net->in_scale, w.x0,
                                                                        nullptr, 0);
-    if (cudaGetLastError() != cudaSuccess) return fp_fail(FP_ECUDA, "fp_surrogate_infer: input kernel launch");
+    if (cudaGetLastError() != cudaSuccess) return fp_fail(FP_ECUDA, "%s: input kernel launch", who);
     const __nv_bfloat16* x = w.x0;
     for (int l = 0; l < FP_SUR_LAYERS; ++l) {
         EpiParams P = epi0(d_err);
@@ -662,10 +712,58 @@ int fp_surrogate_infer(const fp_surrogate* net, const float* d_x, int q, float* 
             P.ldf = FP_SUR_OUT;
             P.oshift = net->out_shift;
             P.oscale = net->out_scale;
-            rc = gemm(EPI_OUT_INFER, 160, x, KL[l], net->W[l], KL[l], q, NL[l], KL[l], P, st);
+            P.rowacc = rowacc;
+            rc = gemm(rowacc ? EPI_OUT_ENSEMBLE : EPI_OUT_INFER, 160, x, KL[l], net->W[l], KL[l], q, NL[l], KL[l], P,
+                      st);
         }
-        if (rc != FP_OK) return fp_fail(rc, "fp_surrogate_infer: layer %d GEMM launch failed", l);
+        if (rc != FP_OK) return fp_fail(rc, "%s: layer %d GEMM launch failed", who, l);
     }
+    return FP_OK;
+}
+
+int fp_surrogate_infer(const fp_surrogate* net, const float* d_x, int q, float* d_y, void* d_work,
+                       unsigned long long work_bytes, int* d_err, void* stream) {
+    if (!net || !d_x || !d_y || !d_work) return fp_fail(FP_EINVAL, "fp_surrogate_infer: NULL argument");
+    if (q < 0) return fp_fail(FP_EINVAL, "fp_surrogate_infer: q=%d", q);
+    if (q == 0) return FP_OK;
+    if (work_bytes < infer_ws(q, nullptr, nullptr))
+        return fp_fail(FP_EINVAL, "fp_surrogate_infer: workspace %llu < %zu bytes", work_bytes,
+                       infer_ws(q, nullptr, nullptr));
+    if (!d_err) return fp_fail(FP_EINVAL, "fp_surrogate_infer: d_err is required");
+    InferWs w;
+    infer_ws(q, (unsigned char*)d_work, &w);
+    return infer_member(net, d_x, q, d_y, w, d_err, nullptr, (cudaStream_t)stream, "fp_surrogate_infer");
+}
+
+// spread[r] = sqrt(sum |y0 - y1|^2) / (2 sqrt(sum |mean|^2))
+__global__ void ensemble_spread_kernel(const float* __restrict__ rowacc, int q, float* __restrict__ spread) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= q) return;
+    spread[r] = sqrtf(rowacc[2 * r]) / (2.f * fmaxf(sqrtf(rowacc[2 * r + 1]), 1e-30f));
+}
+
+int fp_surrogate_infer_ensemble(const fp_surrogate* net0, const fp_surrogate* net1, const float* d_x, int q,
+                                float* d_mean, float* d_spread, void* d_work, unsigned long long work_bytes,
+                                int* d_err, void* stream) {
+    if (!net0 || !net1 || !d_x || !d_mean || !d_spread || !d_work || !d_err)
+        return fp_fail(FP_EINVAL, "fp_surrogate_infer_ensemble: NULL argument");
+    if (q < 0) return fp_fail(FP_EINVAL, "fp_surrogate_infer_ensemble: q=%d", q);
+    if (q == 0) return FP_OK;
+    const size_t base = infer_ws(q, nullptr, nullptr), need = base + al256((size_t)q * 2 * sizeof(float));
+    if (work_bytes < need)
+        return fp_fail(FP_EINVAL, "fp_surrogate_infer_ensemble: workspace %llu < %zu bytes", work_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    InferWs w;
+    infer_ws(q, (unsigned char*)d_work, &w);
+    float* rowacc = (float*)((unsigned char*)d_work + base);
+    if (cudaMemsetAsync(rowacc, 0, (size_t)q * 2 * sizeof(float), st) != cudaSuccess)
+        return fp_fail(FP_ECUDA, "fp_surrogate_infer_ensemble: memset");
+    int rc = infer_member(net0, d_x, q, d_mean, w, d_err, nullptr, st, "fp_surrogate_infer_ensemble");
+    if (rc != FP_OK) return rc;
+    rc = infer_member(net1, d_x, q, d_mean, w, d_err, rowacc, st, "fp_surrogate_infer_ensemble");
+    if (rc != FP_OK) return rc;
+    ensemble_spread_kernel<<<(q + 255) / 256, 256, 0, st>>>(rowacc, q, d_spread);
+    if (cudaGetLastError() != cudaSuccess) return fp_fail(FP_ECUDA, "fp_surrogate_infer_ensemble: spread kernel");
     return FP_OK;
 }
 

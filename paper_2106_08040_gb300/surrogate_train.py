@@ -66,12 +66,22 @@ class Ensemble:
     def __init__(self, members):
         self.members = members
 
-    def infer(self, x):
-        ys = [m.infer(x) for m in self.members]
-        mean = sum(ys) / len(ys)
+    def infer(self, x, stream=None):
+        """Mean and spread in one pass (fp_surrogate_infer_ensemble)."""
+        import ctypes as C
         import torch
-        spread = torch.linalg.vector_norm(ys[0] - ys[1], dim=1) / (
-            2.0 * torch.linalg.vector_norm(mean, dim=1).clamp_min(1e-30))
+        from . import _lib
+        a, b = self.members
+        q = x.shape[0]
+        mean = torch.empty((q, surrogate.N_OUT), dtype=torch.float32, device=a.device)
+        spread = torch.empty((q,), dtype=torch.float32, device=a.device)
+        ws = a.workspace(q, 2)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(_lib.lib().fp_surrogate_infer_ensemble(C.byref(a.net), C.byref(b.net), C.c_void_p(x.data_ptr()),
+                                                          int(q), C.c_void_p(mean.data_ptr()),
+                                                          C.c_void_p(spread.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                                          C.c_ulonglong(ws.numel()), C.c_void_p(a._err.data_ptr()),
+                                                          C.c_void_p(s.cuda_stream)), "fp_surrogate_infer_ensemble")
         return mean, spread
 
     def save(self, path, **meta):

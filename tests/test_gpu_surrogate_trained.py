@@ -66,3 +66,26 @@ def test_trained_surrogate_error_and_gain(mods):
     torch.cuda.synchronize()
     t_query = e0.elapsed_time(e1) * 1e-3 / 5 / xb.shape[0]
     assert t_solver / t_query > 1e3, (t_solver, t_query)
+
+
+def test_fused_ensemble_matches_two_member_passes(mods):
+    """fp_surrogate_infer_ensemble (mean and spread folded into the second
+    member's last epilogue) against two fp_surrogate_infer passes combined on
+    the host in FP64, on a query count that is not a multiple of the 128-row
+    tiles: the mean to FP32 rounding of (y0 + y1) / 2, the spread to 1e-5
+    (FP32 sums of 800 squares in a different order)."""
+    fp, surrogate, stt = mods
+    ens = stt.Ensemble.load(stt.DEFAULT_OUT)
+    rng = np.random.default_rng(4)
+    draw = workloads.uneven_sweep_instances(1000, 16, seed=17)
+    x = torch.from_numpy(surrogate.features(draw).astype(np.float32)).cuda()
+    mean, spread = ens.infer(x)
+    y0 = ens.members[0].infer(x).cpu().numpy().astype(np.float64)
+    y1 = ens.members[1].infer(x).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    m_ref = 0.5 * (y0 + y1)
+    s_ref = np.linalg.norm(y0 - y1, axis=1) / (2 * np.linalg.norm(m_ref, axis=1))
+    mm = mean.cpu().numpy().astype(np.float64)
+    assert np.abs(mm - m_ref).max() <= 2e-7 * np.abs(m_ref).max()
+    assert np.abs(spread.cpu().numpy() - s_ref).max() <= 1e-5 * s_ref.max()
+    assert ens.members[0].error_flag() == 0 and ens.members[1].error_flag() == 0
