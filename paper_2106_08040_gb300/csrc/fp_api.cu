@@ -69,6 +69,7 @@ int fp_destroy(fp_ctx* ctx) {
     cudaFree(ctx->d_coef4);
     cudaFree(ctx->d_wdiag);
     cudaFree(ctx->d_tw);
+    cudaFree(ctx->d_fac);
     fp_free_tables(&ctx->host);
     delete ctx;
     return FP_OK;
@@ -89,6 +90,9 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
         return fail(FP_EINVAL, "fp_setup: bad tolerances");
     if (tol->stages != 3 && tol->stages != 5)
         return fail(FP_EUNSUPPORTED, "fp_setup: stages=%d (3 or 5 supported)", tol->stages);
+    if (L_max > FP_L_SMEM && tol->stages != 3)
+        return fail(FP_EUNSUPPORTED, "fp_setup: L_max=%d > %d needs 3 stages (the 5-stage factors of blocks of "
+                    "2 L rows do not fit a CTA's registers)", L_max, FP_L_SMEM);
     fp_ctx* c = new (std::nothrow) fp_ctx();
     if (!c) return fail(FP_ENOMEM, "fp_setup: host allocation");
     c->mat = *mat;
@@ -139,6 +143,10 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
     }
     up((void**)&c->d_tw, tw.data(), tw.size() * sizeof(double));
     if (rc != FP_OK) { fp_destroy(c); return rc; }
+    if (L_max > FP_L_SMEM) {         // factor scratch: one slot per SM (one CTA per SM at these degrees)
+        const size_t fb = (size_t)c->num_sms * fp_solver_fac_bytes(3, L_max);
+        if (cudaMalloc((void**)&c->d_fac, fb) != cudaSuccess) { fp_destroy(c); return fail(FP_ENOMEM, "fp_setup: factor scratch"); }
+    }
     // block structure of every degree 2..L_max, packed into one device buffer
     {
         std::vector<FpBlkHost> bl(L_max + 1);
@@ -222,7 +230,8 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     if ((int)sm > max_sm)
         return fail(FP_EUNSUPPORTED, "fp_solve_batch: %zu bytes of shared memory needed, %d available", sm, max_sm);
     int rc = fp_launch_solve(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
-                             d_m, d_dmdt, d_status, d_stats, ctx->num_sms, (cudaStream_t)stream, nullptr, nullptr);
+                             d_m, d_dmdt, d_status, d_stats, ctx->num_sms, (cudaStream_t)stream, nullptr, nullptr,
+                             ctx->d_fac);
     if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }
@@ -242,6 +251,8 @@ int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max, const doub
     if (n == 0) return FP_OK;
     if (!d_inst || !d_dJ_dphihat || !d_grad || !d_status || !h_channels || !d_work)
         return fail(FP_EINVAL, "fp_grad: NULL buffer");
+    if (ctx->L_max > FP_L_SMEM)
+        return fail(FP_EUNSUPPORTED, "fp_grad: the adjoint supports L_max <= %d (context has %d)", FP_L_SMEM, ctx->L_max);
     if (k_max < 0 || k_max >= ctx->drv.samples_per_period) return fail(FP_EINVAL, "fp_grad: k_max=%d", k_max);
     if (C < 1 || C > 4) return fail(FP_EINVAL, "fp_grad: C=%d outside [1, 4]", C);
     const long long need = fp_grad_workspace_bytes(ctx, n);
@@ -387,6 +398,9 @@ extern "C" int fp_grad_noalloc(fp_ctx* ctx, const fp_instance* d_inst, int n, in
     if (!ctx) return fail(FP_EINVAL, "fp_grad_noalloc: NULL ctx");
     if (n < 0) return fail(FP_EINVAL, "fp_grad_noalloc: n < 0");
     if (n == 0) return FP_OK;
+    if (ctx->L_max > FP_L_SMEM)
+        return fail(FP_EUNSUPPORTED, "fp_grad_noalloc: the adjoint supports L_max <= %d (context has %d)", FP_L_SMEM,
+                    ctx->L_max);
     if (!d_inst || !d_dJ_dphihat || !d_grad || !d_status || !h_channels)
         return fail(FP_EINVAL, "fp_grad_noalloc: NULL buffer");
     if (k_max < 0 || k_max >= ctx->drv.samples_per_period)

@@ -9,7 +9,8 @@
 #define FP_HD inline
 #endif
 
-#define FP_L_MAX 16          // largest degree whose factors fit in shared memory
+#define FP_L_MAX 24          // largest supported truncation degree
+#define FP_L_SMEM 16         // largest degree whose factors fit in shared memory (above: global scratch, 3 stages)
 #define FP_NSLOT 19          // coupling slots per target row (see slot map below)
 #define FP_NGL 128           // Gauss-Legendre nodes for the Boltzmann initial state
 
@@ -160,9 +161,12 @@ void fp_gauss_legendre(int n, double* x, double* w);
 // ------------------------------------------------ context and launchers ----
 #include <cuda_runtime.h>
 size_t fp_solver_smem_bytes(int stages, int L);
+size_t fp_solver_fac_bytes(int stages, int L);     // global factor bytes per CTA (0 when they fit in shared memory)
+// d_fac: factor scratch of at least num_sms * fp_solver_fac_bytes(stages, L_launch) bytes when that is nonzero
 int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
-                    int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue);
+                    int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue,
+                    unsigned char* d_fac);
 int fp_upload_constants(const FpRadau* r3, const FpRadau* r5, const double* glx, const double* glw);
 size_t fp_adjoint_smem_bytes(int stages, int L);
 size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec);
@@ -188,6 +192,7 @@ struct fp_ctx {
     DevBlk blk;               // device block structure, all degrees 2..L_max
     void* d_blk_mem;          // one allocation backing blk
     double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
+    unsigned char* d_fac;     // factor scratch for L_max > FP_L_SMEM (num_sms CTAs), else NULL
 };
 
 int fp_fail(int code, const char* fmt, ...);

@@ -46,6 +46,8 @@ struct KArgs {
     int L_launch;
     const int* order;       // queue slot -> instance index (NULL: identity)
     int* queue;             // dynamic work counter, zero at launch (NULL: static round robin)
+    unsigned char* fac;     // global factor scratch (degrees above FP_L_SMEM): fac_stride bytes per CTA
+    size_t fac_stride;
 };
 
 // slot -> scalar group: W, ZR, RZ, RX, RY, GZ, GX, GY
@@ -89,6 +91,8 @@ struct Layout {
     int N, L, nmax;
     size_t y, Z, F, f0, yb, diag, rr, zr, rc, zc, dnv, upv, fr, fc, Xr, Xc, lam, aw, ic, total;
     size_t fsum;
+    bool gfac;              // factors in global memory (degree above FP_L_SMEM); fr, fc are then offsets into it
+    size_t fac_bytes;       // bytes of the factors of one instance
 };
 
 // ADJ adds the adjoint state lambda (N) and one more stage-sized buffer (S N).
@@ -116,20 +120,37 @@ __host__ __device__ inline Layout make_layout(int L) {
     ly.zc = o;   o = al16(o + (size_t)NC * N * 8);
     ly.dnv = o;  o = al16(o + N * FP_NLT * 4);
     ly.upv = o;  o = al16(o + N * FP_NLT * 4);
-    ly.fr = o;   o = al16(o + fsum * 4);
-    ly.fc = o;   o = al16(o + (size_t)NC * fsum * 8);
+    ly.gfac = L > FP_L_SMEM;
+    ly.fac_bytes = al16(fsum * 4) + al16((size_t)NC * fsum * 8);
+    if (ly.gfac) {
+        ly.fr = 0;
+        ly.fc = al16(fsum * 4);
+    } else {
+        ly.fr = o;   o = al16(o + fsum * 4);
+        ly.fc = o;   o = al16(o + (size_t)NC * fsum * 8);
+    }
     ly.Xr = o;   o = al16(o + nm2 * 4);
     ly.Xc = o;   o = al16(o + (size_t)NC * nm2 * 8);
     ly.lam = o;  if (ADJ) o = al16(o + N * 8);
     ly.aw = o;   if (ADJ) o = al16(o + (size_t)S * N * 8);
-    ly.ic = ly.fr;                                     // initial-state scratch aliases the factors
-    size_t ic_end = ly.ic + (size_t)FP_NGL * (L + 1) * 8;
-    ly.total = o > ic_end ? o : al16(ic_end);
+    if (ly.gfac) {                                     // initial-state scratch of its own
+        ly.ic = o;
+        o = al16(o + (size_t)FP_NGL * (L + 1) * 8);
+        ly.total = o;
+    } else {
+        ly.ic = ly.fr;                                 // initial-state scratch aliases the factors
+        size_t ic_end = ly.ic + (size_t)FP_NGL * (L + 1) * 8;
+        ly.total = o > ic_end ? o : al16(ic_end);
+    }
     return ly;
 }
 
 size_t fp_solver_smem_bytes(int stages, int L) {
     return stages == 5 ? make_layout<5>(L).total : make_layout<3>(L).total;
+}
+size_t fp_solver_fac_bytes(int stages, int L) {
+    const Layout ly = stages == 5 ? make_layout<5>(L) : make_layout<3>(L);
+    return ly.gfac ? ly.fac_bytes : 0;
 }
 size_t fp_adjoint_smem_bytes(int stages, int L) {
     return stages == 5 ? make_layout<5, true>(L).total : make_layout<3, true>(L).total;
@@ -274,90 +295,124 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 }
 
 // A group of GW warps assembles the Schur-complement block
-// D~_mu = D_mu - C_mu X_{mu-1} of one system (lane = row, warp gw owns the
-// columns [gw*CPW, gw*CPW + CPW)) and inverts it in place by Gauss-Jordan with
-// partial pivoting: the warp owning pivot column k picks the pivot row and
-// publishes the column multipliers through shared memory, one named barrier
-// per pivot.  The inverse is stored column-major (out[c * n + r] = Inv[r][c]).
-// n <= 32.
-template <class T, int S, int GW>
+// D~_mu = D_mu - C_mu X_{mu-1} of one system (lane = row, RS row slots per
+// lane: rows lane + 32 s, warp gw owns the columns [gw*CPW, gw*CPW + CPW)) and
+// inverts it in place by Gauss-Jordan with partial pivoting: the warp owning
+// pivot column k picks the pivot row and publishes the column multipliers
+// through shared memory, one named barrier per pivot.  The inverse is stored
+// column-major (out[c * ldb(n) + r] = Inv[r][c]).  n <= 32 RS.
+template <class T, int S, int GW, int RS = 1>
 __device__ void group_factor_block(Ctx<S>& C, int mu, T shift, const float* gs, float h, const T* Xprev, T* out,
                                    int* pp, T* colbuf, int gw, int barid) {
-    constexpr int CPW = 32 / GW;
+    constexpr int NB = 32 * RS;             // largest block (rows and columns)
+    constexpr int CPW = NB / GW;
+    constexpr unsigned RMASK = (unsigned)NB - 1u;
     const int lane = threadIdx.x & 31;
     const int L = C.L, n = nblk(mu, L), bo = C.boff[mu];
     const int j0 = gw * CPW;
-    T a[CPW];
-    if (lane < n) {
-        const int b = bo + lane;
-        const int g = __ldg(C.glob + b);
-        const T dv = cadd_real(shift, (float)(-(double)h * C.diag[g]));
-        int ks[FP_NSB];
-        float vs[FP_NSB];
+    T a[RS][CPW];
+    bool used[RS];
+    int myk[RS];
 #pragma unroll
-        for (int p = 0; p < FP_NSB; ++p) {
-            ks[p] = __ldg(C.sb_k + b * FP_NSB + p);
-            vs[p] = ks[p] == 255 ? 0.f : gs[__ldg(C.sb_g + b * FP_NSB + p)] * __ldg(C.sb_cf + b * FP_NSB + p);
-        }
-        int kd[FP_NLT];
-        float vd[FP_NLT];
+    for (int s = 0; s < RS; ++s) {
+        const int r = lane + 32 * s;
+        used[s] = r >= n;
+        myk[s] = -1;
+        if (r < n) {
+            const int b = bo + r;
+            const int g = __ldg(C.glob + b);
+            const T dv = cadd_real(shift, (float)(-(double)h * C.diag[g]));
+            int ks[FP_NSB];
+            float vs[FP_NSB];
 #pragma unroll
-        for (int p = 0; p < FP_NLT; ++p) {
-            kd[p] = mu > 0 ? __ldg(C.dn_k + b * FP_NLT + p) : 255;
-            vd[p] = kd[p] == 255 ? 0.f : C.dnv[b * FP_NLT + p];
-        }
-#pragma unroll
-        for (int jj = 0; jj < CPW; ++jj) {
-            const int j = j0 + jj;
-            T v = j == lane ? dv : czero<T>();
-            if (j < n) {
-#pragma unroll
-                for (int p = 0; p < FP_NSB; ++p) v = cadd_real(v, ks[p] == j ? vs[p] : 0.f);
-#pragma unroll
-                for (int p = 0; p < FP_NLT; ++p)
-                    if (kd[p] != 255) v = cfma(-vd[p], Xprev[kd[p] * n + j], v);
+            for (int p = 0; p < FP_NSB; ++p) {
+                ks[p] = __ldg(C.sb_k + b * FP_NSB + p);
+                vs[p] = ks[p] == 255 ? 0.f : gs[__ldg(C.sb_g + b * FP_NSB + p)] * __ldg(C.sb_cf + b * FP_NSB + p);
             }
-            a[jj] = v;
-        }
-    } else {
+            int kd[FP_NLT];
+            float vd[FP_NLT];
 #pragma unroll
-        for (int jj = 0; jj < CPW; ++jj) a[jj] = cadd_real(czero<T>(), j0 + jj == lane ? 1.f : 0.f);
+            for (int p = 0; p < FP_NLT; ++p) {
+                kd[p] = mu > 0 ? __ldg(C.dn_k + b * FP_NLT + p) : 255;
+                vd[p] = kd[p] == 255 ? 0.f : C.dnv[b * FP_NLT + p];
+            }
+#pragma unroll
+            for (int jj = 0; jj < CPW; ++jj) {
+                const int j = j0 + jj;
+                T v = j == r ? dv : czero<T>();
+                if (j < n) {
+#pragma unroll
+                    for (int p = 0; p < FP_NSB; ++p) v = cadd_real(v, ks[p] == j ? vs[p] : 0.f);
+#pragma unroll
+                    for (int p = 0; p < FP_NLT; ++p)
+                        if (kd[p] != 255) v = cfma(-vd[p], Xprev[kd[p] * n + j], v);
+                }
+                a[s][jj] = v;
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < CPW; ++jj) a[s][jj] = cadd_real(czero<T>(), j0 + jj == r ? 1.f : 0.f);
+        }
     }
-    bool used = lane >= n;
-    int myk = -1;
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
         const int owner = k / CPW, kk = k - owner * CPW;
-        T* cb = colbuf + (k & 1) * 32;
+        T* cb = colbuf + (k & 1) * NB;
         if (gw == owner) {
-            const T ak = tree_pick<T, CPW>(a, kk);
-            const float v = used ? 0.f : cabs1(ak);
-            unsigned key = (__float_as_uint(v) & ~31u) | (unsigned)lane;
+            T ak[RS];
+            unsigned key = 0u;
+#pragma unroll
+            for (int s = 0; s < RS; ++s) {
+                ak[s] = tree_pick<T, CPW>(a[s], kk);
+                const float v = used[s] ? 0.f : cabs1(ak[s]);
+                key = max(key, (__float_as_uint(v) & ~RMASK) | (unsigned)(lane + 32 * s));
+            }
             key = __reduce_max_sync(FULLMASK, key);
-            const int p = (int)(key & 31u);
-            const T pinv = crecip(cshfl(ak, p));
-            cb[lane] = lane == p ? pinv : cneg(cmul(ak, pinv));
+            const int p = (int)(key & RMASK);
+            T akp = ak[0];
+#pragma unroll
+            for (int s = 1; s < RS; ++s) akp = (p >> 5) == s ? ak[s] : akp;
+            const T pinv = crecip(cshfl(akp, p & 31));
+#pragma unroll
+            for (int s = 0; s < RS; ++s) {
+                const int r = lane + 32 * s;
+                cb[r] = r == p ? pinv : cneg(cmul(ak[s], pinv));
+            }
             if (lane == 0) pp[k] = p;
         }
         named_bar(barid, 32 * GW);
         const int p = pp[k];
-        const T mlt = cb[lane];                 // pinv on the pivot row, -a_ik / a_pk elsewhere
-        const bool ispiv = lane == p;
+        const int ps = p >> 5, pl = p & 31;
+        T mlt[RS];                               // pinv on the pivot row, -a_ik / a_pk elsewhere
+#pragma unroll
+        for (int s = 0; s < RS; ++s) mlt[s] = cb[lane + 32 * s];
 #pragma unroll
         for (int jj = 0; jj < CPW; ++jj) {
-            const T prj = cshfl(a[jj], p);
-            const T upd = ispiv ? cmul(prj, mlt) : cfma(mlt, prj, a[jj]);
-            a[jj] = (j0 + jj == k) ? mlt : upd;
+            T src = a[0][jj];
+#pragma unroll
+            for (int s = 1; s < RS; ++s) src = ps == s ? a[s][jj] : src;
+            const T prj = cshfl(src, pl);
+#pragma unroll
+            for (int s = 0; s < RS; ++s) {
+                const bool ispiv = lane + 32 * s == p;
+                const T upd = ispiv ? cmul(prj, mlt[s]) : cfma(mlt[s], prj, a[s][jj]);
+                a[s][jj] = (j0 + jj == k) ? mlt[s] : upd;
+            }
         }
-        if (ispiv) { used = true; myk = k; }
-    }
-    if (lane < n && myk >= 0) {
 #pragma unroll
-        for (int jj = 0; jj < CPW; ++jj) {
-            const int j = j0 + jj;
-            if (j < n) {
-                const int pj = pp[j];
-                if (pj < n) out[pj * ldb(n) + myk] = a[jj];  // pj >= n only for a singular block
+        for (int s = 0; s < RS; ++s)
+            if (lane + 32 * s == p) { used[s] = true; myk[s] = k; }
+    }
+#pragma unroll
+    for (int s = 0; s < RS; ++s) {
+        if (lane + 32 * s < n && myk[s] >= 0) {
+#pragma unroll
+            for (int jj = 0; jj < CPW; ++jj) {
+                const int j = j0 + jj;
+                if (j < n) {
+                    const int pj = pp[j];
+                    if (pj < n) out[pj * ldb(n) + myk[s]] = a[s][jj];  // pj >= n only for a singular block
+                }
             }
         }
     }
@@ -366,21 +421,27 @@ __device__ void group_factor_block(Ctx<S>& C, int mu, T shift, const float* gs, 
 // X_mu = Inv_mu B_mu (n x n2, row-major) for one system; one warp per column c
 // (lane = row r).  B_mu[k][c] is the coupling of row k (block mu) to row c
 // (block mu+1), reached through the dn list of row c and its back pointer.
-template <class T, int S>
+template <class T, int S, int RS = 1>
 __device__ __forceinline__ void x_column(Ctx<S>& C, int mu, int c, const T* inv, T* X) {
     const int lane = threadIdx.x & 31;
     const int L = C.L, n = nblk(mu, L), n2 = nblk(mu + 1, L);
     const int bc = C.boff[mu + 1] + c, bo = C.boff[mu];
-    T acc = czero<T>();
+    T acc[RS];
+#pragma unroll
+    for (int s = 0; s < RS; ++s) acc[s] = czero<T>();
 #pragma unroll
     for (int p = 0; p < FP_NLT; ++p) {
         const int k = __ldg(C.dn_k + bc * FP_NLT + p);
         if (k == 255) continue;
         const int q = __ldg(C.dnT + bc * FP_NLT + p);
         const float bv = q == 255 ? 0.f : C.upv[(bo + k) * FP_NLT + q];
-        if (lane < n) acc = cfma(bv, inv[k * ldb(n) + lane], acc);
+#pragma unroll
+        for (int s = 0; s < RS; ++s)
+            if (lane + 32 * s < n) acc[s] = cfma(bv, inv[k * ldb(n) + lane + 32 * s], acc[s]);
     }
-    if (lane < n) X[lane * n2 + c] = acc;
+#pragma unroll
+    for (int s = 0; s < RS; ++s)
+        if (lane + 32 * s < n) X[(lane + 32 * s) * n2 + c] = acc[s];
 }
 
 template <int S> struct Groups {
@@ -389,7 +450,12 @@ template <int S> struct Groups {
     static constexpr int GW = NWARP / NSYS >= 4 ? 4 : (NWARP / NSYS >= 2 ? 2 : 1);   // warps per system
 };
 
-template <int S>
+// per-system scratch of the factorisation: pivot rows (FP_PP_SYS ints) and the
+// double-buffered multiplier column (FP_CB_SYS entries), sized for 64-row blocks
+#define FP_PP_SYS 64
+#define FP_CB_SYS 128
+
+template <int S, int RS = 1>
 __device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2* colbuf) {
     constexpr int NC = Groups<S>::NC;
     constexpr int NSYS = Groups<S>::NSYS;
@@ -409,23 +475,23 @@ __device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2*
     const size_t nm2 = (size_t)C.ly.nmax * C.ly.nmax;
     for (int mu = 0; mu <= L; ++mu) {
         if (sys == 0) {
-            group_factor_block<float, S, GW>(C, mu, (float)RAD<S>().gam, gs, (float)h, C.Xr, C.fr + C.foff[mu],
-                                             pp, (float*)colbuf, gw, 1);
+            group_factor_block<float, S, GW, RS>(C, mu, (float)RAD<S>().gam, gs, (float)h, C.Xr, C.fr + C.foff[mu],
+                                                 pp, (float*)colbuf, gw, 1);
         } else if (sys <= NC) {
             const int q = sys - 1;
             const float2 shift = make_float2((float)RAD<S>().alp[q], -(float)RAD<S>().bet[q]);
-            group_factor_block<float2, S, GW>(C, mu, shift, gs, (float)h, C.Xc + q * nm2,
-                                              C.fc + (size_t)q * C.ly.fsum + C.foff[mu], pp + 32 * sys,
-                                              colbuf + 64 * sys, gw, 1 + sys);
+            group_factor_block<float2, S, GW, RS>(C, mu, shift, gs, (float)h, C.Xc + q * nm2,
+                                                  C.fc + (size_t)q * C.ly.fsum + C.foff[mu], pp + FP_PP_SYS * sys,
+                                                  colbuf + FP_CB_SYS * sys, gw, 1 + sys);
         }
         __syncthreads();
         if (mu < L) {
             const int n2 = nblk(mu + 1, L);
             for (int item = w; item < NSYS * n2; item += NWARP) {
                 const int sy = item / n2, c = item - sy * n2;
-                if (sy == 0) x_column<float, S>(C, mu, c, C.fr + C.foff[mu], C.Xr);
-                else x_column<float2, S>(C, mu, c, C.fc + (size_t)(sy - 1) * C.ly.fsum + C.foff[mu],
-                                         C.Xc + (sy - 1) * nm2);
+                if (sy == 0) x_column<float, S, RS>(C, mu, c, C.fr + C.foff[mu], C.Xr);
+                else x_column<float2, S, RS>(C, mu, c, C.fc + (size_t)(sy - 1) * C.ly.fsum + C.foff[mu],
+                                             C.Xc + (sy - 1) * nm2);
             }
             __syncthreads();
         }
@@ -437,12 +503,13 @@ __device__ void factorize(Ctx<S>& C, const AScal& sc, double h, int* pp, float2*
 // of GW warps: row r of a block is handled by GW lanes (r = gw*RPW + lane%RPW,
 // part = lane/RPW) that split the matvec columns and reduce with shuffles.
 // rhs (block order) is overwritten; the solution ends in z.
-template <class T, int S, int GW, bool TRANS>
+template <class T, int S, int GW, bool TRANS, int RS = 1>
 __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, int gw, int barid) {
     // TRANS solves M^T x = b with the same factors: the forward sweep uses
     // B^T (values reached through dnT), the backward sweep C^T (through upT) and
     // the block inverses transposed.
-    constexpr int RPW = 32 / GW;
+    constexpr int RPW = 32 * RS / GW;       // rows per warp (GW warps cover blocks of up to 32 RS rows)
+    static_assert(RPW <= 32, "a warp holds at most 32 rows");
     const int lane = threadIdx.x & 31;
     const int rl = lane % RPW, part = lane / RPW, r = gw * RPW + rl;
     const int L = C.L;
@@ -599,8 +666,8 @@ __device__ __forceinline__ double sample_time(const fp_drive& d, int j) {
 template <int S>
 struct Shared {
     int boff[FP_L_MAX + 2], foff[FP_L_MAX + 2];
-    int pp[32 * (1 + (S - 1) / 2)];
-    float2 colbuf[64 * (1 + (S - 1) / 2)];
+    int pp[FP_PP_SYS * (1 + (S - 1) / 2)];
+    float2 colbuf[FP_CB_SYS * (1 + (S - 1) / 2)];
     float red[NWARP];
     double dred[NWARP * 12];
     double R[9], off[3], dm[4];          // dm[3]: |<m>|^2 of the last written sample
@@ -609,7 +676,7 @@ struct Shared {
 };
 
 template <int S, bool ADJ>
-__device__ void bind_smem(Ctx<S>& C, unsigned char* smem, int L_launch, Shared<S>& sh) {
+__device__ void bind_smem(Ctx<S>& C, unsigned char* smem, int L_launch, Shared<S>& sh, unsigned char* fac) {
     C.ly = make_layout<S, ADJ>(L_launch);
     C.y = (double*)(smem + C.ly.y);
     C.Z = (double*)(smem + C.ly.Z);
@@ -623,8 +690,9 @@ __device__ void bind_smem(Ctx<S>& C, unsigned char* smem, int L_launch, Shared<S
     C.zc = (float2*)(smem + C.ly.zc);
     C.dnv = (float*)(smem + C.ly.dnv);
     C.upv = (float*)(smem + C.ly.upv);
-    C.fr = (float*)(smem + C.ly.fr);
-    C.fc = (float2*)(smem + C.ly.fc);
+    unsigned char* fb = C.ly.gfac ? fac : smem;       // factors: shared memory, or this CTA's global scratch
+    C.fr = (float*)(fb + C.ly.fr);
+    C.fc = (float2*)(fb + C.ly.fc);
     C.Xr = (float*)(smem + C.ly.Xr);
     C.Xc = (float2*)(smem + C.ly.Xc);
     C.lam = (double*)(smem + C.ly.lam);
@@ -679,7 +747,7 @@ __device__ FpParams setup_instance(Ctx<S>& C, const KArgs& A, const fp_instance&
 // guess already set) of the step (t, hs) from C.y; stage scalars in sh.scj.
 struct NewtonResult { bool conv, nonfinite; float theta, dmax; int iters; };
 
-template <int S>
+template <int S, int RS = 1>
 __device__ NewtonResult newton_stages(Ctx<S>& C, const DevTab& T, double hs, double h_f, double sc_err, float& eta,
                                       float kappa, int maxit, Shared<S>& sh) {
     constexpr int NC = (S - 1) / 2;
@@ -727,10 +795,10 @@ __device__ NewtonResult newton_stages(Ctx<S>& C, const DevTab& T, double hs, dou
         {
             constexpr int GW = Groups<S>::GW;
             const int sys = w / GW, gw = w - sys * GW;
-            if (sys == 0) group_solve<float, S, GW, false>(C, C.fr, C.rr, C.zr, gw, 1);
+            if (sys == 0) group_solve<float, S, GW, false, RS>(C, C.fr, C.rr, C.zr, gw, 1);
             else if (sys <= NC)
-                group_solve<float2, S, GW, false>(C, C.fc + (size_t)(sys - 1) * C.ly.fsum, C.rc + (sys - 1) * N,
-                                                  C.zc + (sys - 1) * N, gw, 1 + sys);
+                group_solve<float2, S, GW, false, RS>(C, C.fc + (size_t)(sys - 1) * C.ly.fsum, C.rc + (sys - 1) * N,
+                                                      C.zc + (sys - 1) * N, gw, 1 + sys);
         }
         __syncthreads();
         // Z += T dW (h_f / h)
@@ -830,9 +898,9 @@ __device__ void predict_stages(Ctx<S>& C, bool pred, Shared<S>& sh) {
 
 // factorise the iteration matrices for step hs with the operator scalars sc of
 // its end point (stage S of the step, c_S = 1)
-template <int S>
+template <int S, int RS = 1>
 __device__ void refactor_at(Ctx<S>& C, const AScal& sc, double hs, Shared<S>& sh) {
-    factorize<S>(C, sc, hs, sh.pp, sh.colbuf);
+    factorize<S, RS>(C, sc, hs, sh.pp, sh.colbuf);
 }
 
 // factorise the iteration matrices for step hs ending at t + hs
@@ -859,7 +927,7 @@ __device__ void refactor(Ctx<S>& C, const KArgs& A, const FpParams& P, const dou
 #define FP_REC 5            // doubles recorded per accepted step
 struct FwdOut { int status, nsteps, nrej, nit, nfac; };
 
-template <int S, bool REC>
+template <int S, bool REC, int RS = 1>
 __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const FpParams& P, Shared<S>& sh,
                                    double* rec_steps, double* rec_ckpt, int max_rec) {
     const DevTab& T = A.tab;
@@ -871,6 +939,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
     double B[3];
     field_nframe(A, R, off, 0.0, B);
     initial_state<S>(C, P, B, (unsigned char*)C.y - C.ly.y, C.y);
+    static_assert(!(REC && RS != 1), "the adjoint records steps of the single-slot factorisation only");
 
     const double T_s = A.drv.period / A.drv.samples_per_period;     // sample spacing = h_max
     const double rtol = A.tol.rtol, atol = A.tol.atol;
@@ -939,7 +1008,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         const AScal s_end = sh.scj[S - 1];           // operator scalars at t + hs (c_S = 1)
         const double rat = fac_valid ? hs / h_f : 0.0;
         if (!fac_valid || force_refac || rat < FP_HRAT_LO || rat > FP_HRAT_HI || since_fac >= A.tol.refactor_every) {
-            refactor_at<S>(C, s_end, hs, sh);
+            refactor_at<S, RS>(C, s_end, hs, sh);
             h_f = hs; t_f = t; fac_valid = true; force_refac = false; since_fac = 0; ++out.nfac;
         }
         if (REC && out.nsteps % FP_CKPT == 0) {       // checkpoint the state before this step
@@ -948,7 +1017,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         }
         predict_stages<S>(C, have_pred, sh);
         const double sc_err = atol + rtol * ymax;
-        const NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_err, eta, FP_KAPPA, A.tol.newton_max_iter, sh);
+        const NewtonResult nr = newton_stages<S, RS>(C, T, hs, h_f, sc_err, eta, FP_KAPPA, A.tol.newton_max_iter, sh);
         out.nit += nr.iters;
         if (nr.nonfinite) { out.status = FP_STATUS_NONFINITE; break; }
         if (!nr.conv) {
@@ -970,7 +1039,7 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
         }
         __syncthreads();
         if ((threadIdx.x >> 5) < Groups<S>::GW)
-            group_solve<float, S, Groups<S>::GW, false>(C, C.fr, C.rr, C.zr, threadIdx.x >> 5, 1);
+            group_solve<float, S, Groups<S>::GW, false, RS>(C, C.fr, C.rr, C.zr, threadIdx.x >> 5, 1);
         __syncthreads();
         float em = 0.f;
         const float escale = (float)(RAD<S>().gam * h_f / hs);
@@ -1020,12 +1089,12 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
     return out;
 }
 
-template <int S>
+template <int S, int RS>
 __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared<S> sh;
     Ctx<S> C;
-    bind_smem<S, false>(C, smem, A.L_launch, sh);
+    bind_smem<S, false>(C, smem, A.L_launch, sh, A.fac ? A.fac + (size_t)blockIdx.x * A.fac_stride : nullptr);
     __shared__ int s_slot;
     // instances come either round robin (slot = blockIdx.x + k gridDim.x) or,
     // with a work counter, one at a time in the caller's order, so CTAs that
@@ -1055,7 +1124,7 @@ __global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
             continue;
         }
         const FpParams P = setup_instance<S>(C, A, in, sh);
-        const FwdOut o = forward_instance<S, false>(C, A, inst, P, sh, nullptr, nullptr, 0);
+        const FwdOut o = forward_instance<S, false, RS>(C, A, inst, P, sh, nullptr, nullptr, 0);
         if (threadIdx.x == 0) {
             A.status[inst] = o.status;
             if (A.stats) {
@@ -1362,7 +1431,7 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
     const KArgs& A = G.A;
     const DevTab& T = A.tab;
     Ctx<S> C;
-    bind_smem<S, true>(C, smem, A.L_launch, sh);
+    bind_smem<S, true>(C, smem, A.L_launch, sh, nullptr);
     const int Sp = A.drv.samples_per_period, j0 = A.S_out - Sp;
     const int Nmax = (A.L_launch + 1) * (A.L_launch + 1);
     double* ws = G.work + (size_t)blockIdx.x * G.work_per_cta;
@@ -1594,7 +1663,8 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
 // --------------------------------------------------------- host launch ----
 int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
-                    int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue) {
+                    int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue,
+                    unsigned char* d_fac) {
     KArgs A;
     A.order = d_order;
     A.queue = d_queue;
@@ -1611,29 +1681,44 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
     A.stats = d_stats;
     A.S_out = drv->output_periods * drv->samples_per_period;
     A.L_launch = L_launch;
+    A.fac = nullptr;
+    A.fac_stride = 0;
     cudaError_t e;
-    if (stages == 5) {
-        const size_t sm = fp_solver_smem_bytes(5, L_launch);
-        e = cudaFuncSetAttribute(fp_solve_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (L_launch > FP_L_SMEM) {
+        // blocks of up to 2 L_launch <= 64 rows (two row slots per lane), factors in
+        // this launch's global scratch, one CTA per SM (one scratch slot each)
+        if (stages != 3 || !d_fac) return FP_EUNSUPPORTED;
+        A.fac = d_fac;
+        A.fac_stride = fp_solver_fac_bytes(3, L_launch);
+        const size_t sm = fp_solver_smem_bytes(3, L_launch);
+        e = cudaFuncSetAttribute(fp_solve_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return FP_ECUDA;
         const int grid = n < num_sms ? n : num_sms;
-        fp_solve_kernel<5><<<grid, NT, sm, st>>>(A);
+        fp_solve_kernel<3, 2><<<grid, NT, sm, st>>>(A);
+        return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
+    }
+    if (stages == 5) {
+        const size_t sm = fp_solver_smem_bytes(5, L_launch);
+        e = cudaFuncSetAttribute(fp_solve_kernel<5, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return FP_ECUDA;
+        const int grid = n < num_sms ? n : num_sms;
+        fp_solve_kernel<5, 1><<<grid, NT, sm, st>>>(A);
         return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
     }
     // stages 3: as many CTAs per SM as registers and shared memory allow
     // (one at the kernel's register budget)
     const size_t sm = make_layout<3>(L_launch).total;
     int per_sm = 0;
-    cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(fp_solve_kernel<3, 1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
-    e = cudaFuncSetAttribute(fp_solve_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(fp_solve_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return FP_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_solve_kernel<3>, NT, sm) != cudaSuccess) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_solve_kernel<3, 1>, NT, sm) != cudaSuccess) per_sm = 1;
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 2) per_sm = 2;
     const int cap = per_sm * num_sms;
     const int grid = n < cap ? n : cap;
-    fp_solve_kernel<3><<<grid, NT, sm, st>>>(A);
+    fp_solve_kernel<3, 1><<<grid, NT, sm, st>>>(A);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
 }
 

@@ -32,6 +32,7 @@ struct FpBucket {
     int stages;
     int refactor_every;
     float tuned_ms;   // autotune time of the chosen candidate (0 if not tuned)
+    unsigned char* d_fac;   // factor scratch of this bucket (degrees above FP_L_SMEM), else NULL
 };
 
 struct fp_sweep {
@@ -70,7 +71,7 @@ int launch_bucket(fp_sweep* sw, int bi, const fp_instance* d_inst, double* d_m, 
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if ((int)sm > max_sm) return fp_fail(FP_EUNSUPPORTED, "fp_sweep: %zu bytes of shared memory at L=%d", sm, bk.L);
     int rc = fp_launch_solve(bk.stages, &tab, &c->blk, &c->mat, &c->drv, &tol, d_inst, count, bk.L, d_m, d_dmdt,
-                             d_status, d_stats, c->num_sms, st, order, queue);
+                             d_status, d_stats, c->num_sms, st, order, queue, bk.d_fac);
     if (rc != FP_OK) return fp_fail(rc, "fp_sweep: launch at L=%d failed: %s", bk.L, cudaGetErrorString(cudaGetLastError()));
     return FP_OK;
 }
@@ -175,9 +176,16 @@ int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_widt
     sw->n = n;
     sw->h_order = idx;
     for (int k = 0, s = 0; k < nbk; s += bc[k], ++k)
-        sw->b.push_back(FpBucket{bL[k], s, bc[k], ctx->tol.stages, ctx->tol.refactor_every, 0.f});
+        sw->b.push_back(FpBucket{bL[k], s, bc[k], bL[k] > FP_L_SMEM ? 3 : ctx->tol.stages, ctx->tol.refactor_every,
+                                 0.f, nullptr});
     const int nb = (int)sw->b.size();
     int rc = FP_OK;
+    // buckets above FP_L_SMEM keep their factors in global memory: one scratch
+    // per bucket (buckets run concurrently on side streams), one slot per SM
+    for (auto& bk : sw->b)
+        if (rc == FP_OK && bk.L > FP_L_SMEM &&
+            cudaMalloc((void**)&bk.d_fac, (size_t)ctx->num_sms * fp_solver_fac_bytes(3, bk.L)) != cudaSuccess)
+            rc = fp_fail(FP_ENOMEM, "fp_sweep_plan: factor scratch at L=%d", bk.L);
     if (cudaMalloc(&sw->d_order, sizeof(int) * n) != cudaSuccess || cudaMalloc(&sw->d_tune, sizeof(int) * n) != cudaSuccess ||
         cudaMalloc(&sw->d_queue, sizeof(int) * nb) != cudaSuccess)
         rc = fp_fail(FP_ENOMEM, "fp_sweep_plan: cudaMalloc");
@@ -205,6 +213,7 @@ int fp_sweep_destroy(fp_sweep* sw) {
     cudaFree(sw->d_order);
     cudaFree(sw->d_tune);
     cudaFree(sw->d_queue);
+    for (auto& bk : sw->b) cudaFree(bk.d_fac);
     for (auto s : sw->side)
         if (s) cudaStreamDestroy(s);
     for (auto e : sw->join)
@@ -284,6 +293,7 @@ int fp_sweep_autotune(fp_sweep* sw, const fp_instance* d_inst, double* d_m, doub
         float best = -1.f;
         int best_c = -1;
         for (int c = 0; c < 4 && rc == FP_OK; ++c) {
+            if (bk.L > FP_L_SMEM && cand[c][0] != 3) continue;     // 3 stages only above FP_L_SMEM
             bk.stages = cand[c][0];
             bk.refactor_every = cand[c][1];
             cudaMemsetAsync(sw->d_queue + bi, 0, sizeof(int), st);

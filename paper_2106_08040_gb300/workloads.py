@@ -130,3 +130,17 @@ def uneven_sweep_instances(n, L, seed=SEED, nxy=64, fov=24e-3, n_dir=16, K_range
     inst["d"] = d_median * np.exp(d_sigma * rng.normal(size=n))
     inst["L"] = L
     return inst
+
+
+def high_degree_workload(L):
+    """One instance resolved only at high truncation degree (barrier sigma ~ 11,
+    d = 22 nm, K = 8e3 J/m^3, easy axis (1.1, 0.4) rad, offset (2, -3, 1) mT)
+    under a 12 mT, 50 kHz drive along x, one period of 64 samples, degree L."""
+    dspec = DriveSpec(amp=(0.012, 0.0, 0.0), freq=(50e3, 50e3, 50e3), phase=(0.0, 0.0, 0.0),
+                      period=2e-5, samples_per_period=64, warmup_periods=0, output_periods=1)
+    inst = make_instances(1)
+    inst["h_off"] = [[0.002, -0.003, 0.001]]
+    inst["theta"], inst["phi"] = 1.1, 0.4
+    inst["K"], inst["d"] = 8e3, 22e-9
+    inst["L"] = L
+    return dspec, inst

@@ -1,12 +1,27 @@
 """GPU parity of the CUDA path (libfp.so through its C ABI) against the FP64 oracle.
 
-Bar: relative L2 error of the magnetization trace <= 1e-9
+Trace bar: relative L2 error of the magnetization trace <= 1e-9
 (||m_gpu - m_oracle||_2 / ||m_oracle||_2 over all samples and components, per
-instance).  d<m>/dt = l = 1 rows of A(t) c amplifies the coefficient error by
-||A|| ~ 1e10 1/s relative to |dm/dt| / |m|, so at the same integrator tolerance
-the derivative, and phi_hat computed from it, carry a larger stated error:
-relative L2 <= 1e-6.  The oracle solves the same Galerkin ODE with an
-independent integrator (rtol 1e-10..1e-12), the GPU runs at rtol 1e-9.
+instance).
+
+Derivative bar, derived (not fitted): d<m>/dt = sqrt(4 pi/3) (A(t_j) c)_{l=1}
+takes the difference of large terms, so a state error dc costs |A_{l=1}| |dc|
+in d<m>/dt while the trace sees only dc_{l=1}.  The integrator keeps the local
+state error of every step below rtol max|c| (max norm) and the operator damps
+every non-conserved mode within a sample interval (relaxation time ~ 26 ns
+against a 400 ns spacing at sigma = 2), so the state error at a sample is at
+most the sum of the local errors of the steps inside the last sample
+interval: G rtol max|c| with G = ceil(accepted steps / samples) from the
+kernel's own counters over the (warm-up + output) sample intervals (2 for
+5 stages, 5 for 3 stages on the Lissajous workload).  How integration errors of the state map into d<m>/dt is measured
+on the oracle alone: its self-convergence between rtol 1e-11 and 1e-12 gives
+the state change eps_c (relative to max|c|) and the d<m>/dt change eps_d,
+an amplification A = eps_d / eps_c.  The bar for a GPU run at rtol r is
+    DTOL(r) = A G r + eps_d,
+the second term bounding the oracle reference's own d<m>/dt error.  phi_hat,
+a linear map of the last period's d<m>/dt, takes the same form with its own
+eps_phi.  The goldens (tests/golden, oracle at rtol 1e-12) store eps_c,
+eps_d and eps_phi; small on-the-fly cases compute them from two oracle solves.
 """
 import glob
 import os
@@ -22,7 +37,21 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD = os.path.join(HERE, "golden")
 TOL = 1e-9          # magnetization trace
-DTOL = 1e-6         # d<m>/dt and phi_hat
+
+
+def dtol(ref, rtol, key="selfconv_dmdt", G=1.0):
+    """Derived bar DTOL(rtol) = (eps_key / eps_c) G rtol + eps_key of an oracle reference."""
+    return float(ref[key]) / float(ref["selfconv_c"]) * G * rtol + float(ref[key])
+
+
+def steps_per_interval(stats, dspec, rows=None):
+    """G = ceil(accepted steps / sample intervals integrated), the largest over the
+    given instances ((warm-up + output periods) x samples per period intervals)."""
+    st = np.asarray(stats.cpu().numpy() if hasattr(stats, "cpu") else stats)
+    if rows is not None:
+        st = st[rows]
+    intervals = (dspec.warmup_periods + dspec.output_periods) * dspec.samples_per_period
+    return float(np.ceil(st[:, 0].max() / intervals))
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +71,17 @@ def oracle_solve(dspec, rec, rtol=1e-11):
     sched = solve.Schedule(dspec.samples_per_period, dspec.warmup_periods, dspec.output_periods)
     inst = solve.Instance(h_off=tuple(rec["h_off"]), theta=float(rec["theta"]), phi=float(rec["phi"]),
                           K=float(rec["K"]), d=float(rec["d"]), L=int(rec["L"]))
-    return solve.solve_instance(physics.Material(), drive, inst, sched, rtol=rtol)
+    return solve.solve_instance(physics.Material(), drive, inst, sched, rtol=rtol, return_state=True)
+
+
+def oracle_reference(dspec, rec, rtol=1e-12, rtol_check=1e-11):
+    """Oracle solution at rtol with the self-convergence figures of the derived
+    bar (a second solve at rtol_check)."""
+    r12 = oracle_solve(dspec, rec, rtol)
+    r11 = oracle_solve(dspec, rec, rtol_check)
+    r12["selfconv_c"] = np.abs(r11["c"] - r12["c"]).max() / np.abs(r12["c"]).max()
+    r12["selfconv_dmdt"] = rel(r11["dmdt"], r12["dmdt"])
+    return r12
 
 
 @pytest.mark.parametrize("stages", [3, 5])
@@ -56,8 +95,9 @@ def test_single_instance_trace(fp, stages):
     m, dm, st, stats = fp.solve(ctx, inst)
     torch.cuda.synchronize()
     assert int(st[0]) == 0
+    G = steps_per_interval(stats, dspec)
     assert rel(m.cpu().numpy()[0], ref["m"]) <= TOL
-    assert rel(dm.cpu().numpy()[0], ref["dmdt"]) <= DTOL
+    assert rel(dm.cpu().numpy()[0], ref["dmdt"]) <= dtol(ref, 1e-9, G=G)
 
 
 @pytest.mark.parametrize("stages", [3, 5])
@@ -76,8 +116,9 @@ def test_system_matrix_full_launch_sampled_voxels(fp, stages):
     for f in files:
         ref = np.load(f)
         k = int(ref["iy"]) * 32 + int(ref["ix"])
+        G = steps_per_interval(stats, dspec, [k])
         assert rel(mm[k], ref["m"]) <= TOL, f
-        assert rel(dd[k], ref["dmdt"]) <= DTOL, f
+        assert rel(dd[k], ref["dmdt"]) <= dtol(ref, 1e-9, G=G), f
     # mirror symmetry (any size): with n || x, f_x T = 16, f_y T = 17 the field of
     # voxel (x, y) at t + T/2 is R_x(pi) applied to the field of voxel (x, -y) at t,
     # so m_(x,y)(t + T/2) = (m_x, -m_y, -m_z)_(x,-y)(t) in the periodic regime
@@ -101,9 +142,10 @@ def test_ragged_degrees_random_instances(fp):
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == 0).all()
     for i in range(len(inst)):
-        r = oracle_solve(dspec, inst[i], rtol=1e-11)
+        r = oracle_reference(dspec, inst[i])
+        G = steps_per_interval(stats, dspec, [i])
         assert rel(m.cpu().numpy()[i], r["m"]) <= TOL, i
-        assert rel(dm.cpu().numpy()[i], r["dmdt"]) <= DTOL, i
+        assert rel(dm.cpu().numpy()[i], r["dmdt"]) <= dtol(r, 1e-10, G=G), i
 
 
 def test_unresolved_truncation_is_flagged(fp):
@@ -137,12 +179,14 @@ def test_rotation_covariance(fp):
         inst[i]["h_off"] = oo
         inst[i]["theta"], inst[i]["phi"] = np.arccos(nn[2]), np.arctan2(nn[1], nn[0])
     ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-10, stages=3), 10)
-    m, dm, st, _ = fp.solve(ctx, inst)
+    m, dm, st, stats = fp.solve(ctx, inst)
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == 0).all()
     mm, dd = m.cpu().numpy(), dm.cpu().numpy()
+    r = oracle_reference(dspec, inst[0])
+    G = steps_per_interval(stats, dspec)
     assert rel(mm[1], mm[0] @ R.T) <= TOL
-    assert rel(dd[1], dd[0] @ R.T) <= DTOL
+    assert rel(dd[1], dd[0] @ R.T) <= 2 * dtol(r, 1e-10, G=G)   # two GPU solves, each within the bar
 
 
 def test_bad_and_empty_inputs(fp):
@@ -179,6 +223,7 @@ def test_phi_hat_matches_oracle_dft(fp):
     dspec, inst = workloads.system_matrix_workload()
     ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=3), 16)
     m, dm, st, stats = fp.solve(ctx, inst[k:k + 1])
+    G = steps_per_interval(stats, dspec)
     ch = np.array([[1.0, 0, 0], [0, 1.0, 0]])
     out = torch.empty((1, 2, 817, 2), dtype=torch.float64, device=dm.device)
     fp.fp_signal(ctx, dm, 1, 816, ch, out)
@@ -188,4 +233,64 @@ def test_phi_hat_matches_oracle_dft(fp):
     ph_same = osolve.phi_hat(dm.cpu().numpy()[0], ch, 1632, 816)
     assert np.abs(ph - ph_same).max() <= 1e-12 * np.abs(ph_same).max()
     ph_or = osolve.phi_hat(ref["dmdt"], ch, 1632, 816)
-    assert rel(ph, ph_or) <= DTOL
+    assert rel(ph, ph_or) <= dtol(ref, 1e-9, "selfconv_phihat", G=G)
+
+
+def test_tight_tolerance_parity_and_error_against_rtol(fp):
+    """The three golden voxels in one 5-stage launch at rtol 1e-9, 1e-10 and
+    1e-11: trace, d<m>/dt and phi_hat against the oracle (rtol 1e-12) within
+    the derived bars at each tolerance; the errors are printed (-s) for the
+    record of error against rtol."""
+    from oracle import solve as osolve
+    files = sorted(glob.glob(os.path.join(GOLD, "sysmat_L16_v*.npz")))
+    refs = [np.load(f) for f in files]
+    dspec, inst = workloads.system_matrix_workload()
+    ks = [int(r["iy"]) * 32 + int(r["ix"]) for r in refs]
+    ch = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    for rtol in (1e-9, 1e-10, 1e-11):
+        ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=rtol, stages=5), 16)
+        m, dm, st, stats = fp.solve(ctx, inst[ks])
+        ph = torch.empty((len(ks), 2, 817, 2), dtype=torch.float64, device=dm.device)
+        fp.fp_signal(ctx, dm, len(ks), 816, ch, ph)
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
+        mm, dd, pp = m.cpu().numpy(), dm.cpu().numpy(), ph.cpu().numpy()
+        for i, ref in enumerate(refs):
+            G = steps_per_interval(stats, dspec, [i])
+            e_m, e_d = rel(mm[i], ref["m"]), rel(dd[i], ref["dmdt"])
+            e_p = rel(pp[i, ..., 0] + 1j * pp[i, ..., 1], ref["phihat"])
+            print("rtol %.0e voxel (%d,%d) G %d: trace %.2e  dm/dt %.2e (bar %.2e)  phi_hat %.2e (bar %.2e)"
+                  % (rtol, int(ref["ix"]), int(ref["iy"]), G, e_m, e_d, dtol(ref, rtol, G=G), e_p,
+                     dtol(ref, rtol, "selfconv_phihat", G=G)))
+            assert e_m <= TOL
+            assert e_d <= dtol(ref, rtol, G=G)
+            assert e_p <= dtol(ref, rtol, "selfconv_phihat", G=G)
+        ctx.close()
+
+
+@pytest.mark.parametrize("L", [20, 24])
+def test_degrees_above_shared_memory_factors(fp, L):
+    """Truncation degrees 20 and 24 (blocks of up to 2 L = 48 rows, two row slots
+    per lane, FP32 factors in global scratch, 3 stages) against the oracle at
+    the same degree (golden, rtol 1e-11, self-convergence against 1e-10): the
+    high-degree workload (barrier sigma ~ 11, 12 mT drive, one period), with a
+    second instance (sigma ~ 2.8) at degree 14 in the same launch (ragged)."""
+    ref = np.load(os.path.join(GOLD, "highdeg_L%d.npz" % L))
+    dspec, inst = workloads.high_degree_workload(L)
+    low = inst.copy()
+    low["K"], low["L"] = 2e3, 14
+    both = np.concatenate([inst, low])
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-10, stages=3), 24)
+    m, dm, st, stats = fp.solve(ctx, both)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all(), st
+    mm, dd = m.cpu().numpy(), dm.cpu().numpy()
+    G0, G1 = steps_per_interval(stats, dspec, [0]), steps_per_interval(stats, dspec, [1])
+    e_m, e_d = rel(mm[0], ref["m"]), rel(dd[0], ref["dmdt"])
+    print("L %d: trace %.2e, dm/dt %.2e (bar %.2e)" % (L, e_m, e_d, dtol(ref, 1e-10, G=G0)))
+    assert e_m <= TOL
+    assert e_d <= dtol(ref, 1e-10, G=G0)
+    r = oracle_reference(dspec, low[0], 1e-12, 1e-11)
+    assert rel(mm[1], r["m"]) <= TOL
+    assert rel(dd[1], r["dmdt"]) <= dtol(r, 1e-10, G=G1)
+    ctx.close()
