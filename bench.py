@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the uneven-sweep measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
-    p.add_argument("--no-models", action="store_true", help="skip the M0/M1 model measurement")
+    p.add_argument("--no-models", action="store_true", help="skip the M0/M1/M2 model measurement")
+    p.add_argument("--m1-dictionary", type=int, default=96, help="M1 fit: dictionary elements per call")
+    p.add_argument("--m2-tuples", type=int, default=96, help="M2: (D, K) tuples in the dictionary")
     p.add_argument("--sweep-instances", type=int, default=2048)
     return p.parse_args()
 
@@ -392,7 +394,7 @@ def adjoint_leg(fp, dev, n_inst=152):
     return out
 
 
-def models_leg(fp, dev, peak64, Q=96):
+def models_leg(fp, dev, peak64, Q=96, J2=96):
     """Sec. 2.2 models on the system-matrix grid: M0 traces + phi_hat for the
     1024 voxels, and the M1 fit of a Q-element dictionary (8 diameters x 12
     anisotropies at one angle, synthetic phi_hat of the solver's shape) against
@@ -450,7 +452,7 @@ def models_leg(fp, dev, peak64, Q=96):
     del phi, Sm
     # M2 at the paper's shapes: 12 angles, an 11 x 11 voxel grid, J = 8 x 12
     # (D, K) tuples, both channels, rows I_freq (mixing orders up to 20)
-    A2, J2, N2 = 12, 96, 121
+    A2, N2 = 12, 121
     ks = fp.fp_freq_index_set(20, 20, 16, K1 - 1)
     phi2 = torch.randn((A2, J2, N2, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
     a2 = torch.randn((A2, J2, C, K1, 2), dtype=torch.float64, device=dev, generator=gen)
@@ -491,10 +493,9 @@ def sweep_leg(fp, dev, n_inst):
     from paper_2106_08040_gb300 import workloads
     dspec = workloads.drive_lissajous()
     drv = fp.Drive(**dspec.__dict__)
-    draw = workloads.uneven_sweep_instances(2 * n_inst, 16, seed=11)
-    draw = draw[fp.Material().sigma(draw["K"], draw["d"]) <= 12.0][:n_inst]
-    draw["L"] = fp.truncation_degree(draw, drive=drv, L_min=8, L_max=16)
-    ctx = fp.Context(fp.Material(), drv, fp.Tol(rtol=1e-9, stages=3), 16)
+    draw = workloads.uneven_sweep_instances(n_inst, 24, seed=11)
+    draw["L"] = fp.truncation_degree(draw, drive=drv, L_min=8, L_max=24)
+    ctx = fp.Context(fp.Material(), drv, fp.Tol(rtol=1e-9, stages=3), 24)
     n = len(draw)
     S = ctx.num_samples()
     d_inst = fp.instances_to_device(draw, dev)
@@ -520,11 +521,18 @@ def sweep_leg(fp, dev, n_inst):
     ms = e0.elapsed_time(e1)
     status = st.cpu().numpy()
     periods = dspec.warmup_periods + dspec.output_periods
-    out = {"instances": n, "L_hist": {int(k): int(v) for k, v in zip(*np.unique(draw["L"], return_counts=True))},
+    per_L = {}
+    for Lv in np.unique(draw["L"]):
+        sel = draw["L"] == Lv
+        per_L[int(Lv)] = {"instances": int(sel.sum()), "ok": int((status[sel] == 0).sum()),
+                          "unresolved": int((status[sel] == 6).sum()),
+                          "other": int(((status[sel] != 0) & (status[sel] != 6)).sum())}
+    out = {"instances": n, "per_degree": per_L,
            "ms": ms, "instance_periods_per_s": n * periods / (ms * 1e-3), "status_ok": int((status == 0).sum()),
-           "autotune_s": t_tune, "buckets": sw.info(),
-           "workload": "uneven sweep draws (sigma <= 12), L by truncation rule in [8, 16], Lissajous drive, "
-                       "1 warm-up + 1 output period, rtol 1e-9"}
+           "status_unresolved": int((status == 6).sum()), "autotune_s": t_tune, "buckets": sw.info(),
+           "workload": "uneven-sweep distribution (64 x 64 offsets, 16 Fibonacci axes, K log-uniform 5e2-1e4, "
+                       "d log-normal 20 nm), no barrier cap, L by the truncation rule in [8, 24], Lissajous drive, "
+                       "1 warm-up + 1 output period, rtol 1e-9, 3 stages above degree 16"}
     sw.close()
     ctx.close()
     return out
@@ -660,7 +668,7 @@ def run_gpu(args):
         if not args.no_adjoint:
             out["adjoint"] = adjoint_leg(fp, dev)
         if not args.no_models:
-            out["models"] = models_leg(fp, dev, peak / 1e3)
+            out["models"] = models_leg(fp, dev, peak / 1e3, args.m1_dictionary, args.m2_tuples)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

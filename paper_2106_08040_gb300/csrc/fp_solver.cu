@@ -509,6 +509,7 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
     // B^T (values reached through dnT), the backward sweep C^T (through upT) and
     // the block inverses transposed.
     constexpr int RPW = 32 * RS / GW;       // rows per warp (GW warps cover blocks of up to 32 RS rows)
+    constexpr int NPART = 32 / RPW;         // lanes sharing one row's columns
     static_assert(RPW <= 32, "a warp holds at most 32 rows");
     const int lane = threadIdx.x & 31;
     const int rl = lane % RPW, part = lane / RPW, r = gw * RPW + rl;
@@ -537,7 +538,7 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
         T acc = czero<T>();
         if (r < n) {
 #pragma unroll 4
-            for (int c = part; c < n; c += GW)
+            for (int c = part; c < n; c += NPART)
                 acc = cfma(inv[fo + (TRANS ? r * ld + c : c * ld + r)], rhs[bo + c], acc);
         }
 #pragma unroll
@@ -569,7 +570,7 @@ __device__ void group_solve(Ctx<S>& C, const T* __restrict__ inv, T* rhs, T* z, 
         T acc = czero<T>();
         if (r < n) {
 #pragma unroll 4
-            for (int c = part; c < n; c += GW)
+            for (int c = part; c < n; c += NPART)
                 acc = cfma(inv[fo + (TRANS ? r * ld + c : c * ld + r)], rhs[bo + c], acc);
         }
 #pragma unroll

@@ -294,3 +294,25 @@ def test_degrees_above_shared_memory_factors(fp, L):
     assert rel(mm[1], r["m"]) <= TOL
     assert rel(dd[1], r["dmdt"]) <= dtol(r, 1e-10, G=G1)
     ctx.close()
+
+
+def test_two_row_slot_path_matches_single_slot_path(fp):
+    """The same instances (degrees 10, 14, 16) through the factorisation with
+    shared-memory factors and one row slot (context L_max = 16) and through
+    the two-row-slot path with global factors (context L_max = 24): both
+    integrate the same Galerkin system at the same tolerance, so the traces
+    agree within the trace bar and the statuses are OK."""
+    dspec = workloads.DriveSpec(amp=(0.010, 0.004, 0.0), freq=(50e3, 50e3, 50e3), phase=(0.0, 0.7, 0.0),
+                                period=2e-5, samples_per_period=64, warmup_periods=0, output_periods=1)
+    inst = workloads.random_instances(6, 10, seed=21, max_offset=0.006, K_range=(5e2, 3e3))
+    inst["L"] = [10, 14, 16, 16, 14, 10]
+    out = []
+    for Lmax in (16, 24):
+        ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-10, stages=3), Lmax)
+        m, dm, st, _ = fp.solve(ctx, inst)
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all(), (Lmax, st)
+        out.append(m.cpu().numpy())
+        ctx.close()
+    for i in range(len(inst)):
+        assert rel(out[1][i], out[0][i]) <= TOL, i
