@@ -258,7 +258,10 @@ int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
  * returns FP_EINVAL with the sizes in fp_last_error() and launches nothing.
  * The current device must be the context's.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress), so make that first
- * call before any stream capture.  Every call on a device shares the one
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after a reset of the device (cudaDeviceReset, or a primary-context
+ * reset by other code) it is stale, so do not call fp_grad_noalloc on a
+ * device that has been reset since its first call.  Every call on a device shares the one
  * array and overwrites what the previous call left there (nothing in it needs
  * to start at zero): calls whose launches may overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller. */

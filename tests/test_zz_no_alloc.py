@@ -87,6 +87,25 @@ def test_noalloc_matches_fp_grad_on_two_calls(fp):
     ctx.close()
 
 
+def test_noalloc_calls_allocate_no_device_memory(fp):
+    """Free device memory (driver view) is the same after a first and after a
+    second fp_grad_noalloc call: the calls allocate nothing.  Every buffer the
+    test needs exists before the first reading, so torch's caching allocator
+    does not move either."""
+    ctx = context(fp, max_steps=300_000)
+    d_inst, dJ, n = inputs(fp, 7)
+    grad, st, stats = outputs(n)
+    fp.fp_grad_noalloc(ctx, d_inst, n, KMAX, CH, dJ, grad, st, d_stats=stats)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    fp.fp_grad_noalloc(ctx, d_inst, n, KMAX, CH, dJ, grad, st, d_stats=stats)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert (st.cpu().numpy() == 0).all()
+    assert free1 == free0, (free0, free1)
+    ctx.close()
+
+
 def test_noalloc_refuses_an_instance_larger_than_the_array(fp):
     ctx = context(fp, max_steps=2_000_000)
     assert fp.fp_grad_workspace_bytes(ctx, 1) > (32 << 20)
