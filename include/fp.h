@@ -142,7 +142,10 @@ int fp_num_samples(const fp_ctx* ctx);
  *   d_stats [n][4] or NULL accepted steps, rejected steps, Newton iterations,
  *                          factorisations
  * with S = fp_num_samples(ctx).  n == 0 is a no-op.  Instances with a bad L
- * or non-positive K < 0, d <= 0 get FP_STATUS_BAD_INPUT and zero outputs. */
+ * or non-positive K < 0, d <= 0 get FP_STATUS_BAD_INPUT and zero outputs.
+ * The launch uses the context's factor scratch and work counter (allocated
+ * by fp_setup): calls on one context must not overlap in time (issue them on
+ * one stream, or give each stream its own context). */
 int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n,
                    double* d_m, double* d_dmdt, int* d_status, int* d_stats,
                    void* stream);

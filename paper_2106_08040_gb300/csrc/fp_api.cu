@@ -70,6 +70,7 @@ int fp_destroy(fp_ctx* ctx) {
     cudaFree(ctx->d_wdiag);
     cudaFree(ctx->d_tw);
     cudaFree(ctx->d_fac);
+    cudaFree(ctx->d_queue);
     fp_free_tables(&ctx->host);
     delete ctx;
     return FP_OK;
@@ -143,10 +144,11 @@ int fp_setup(const fp_material* mat, const fp_drive* drive, const fp_tol* tol, i
     }
     up((void**)&c->d_tw, tw.data(), tw.size() * sizeof(double));
     if (rc != FP_OK) { fp_destroy(c); return rc; }
-    if (L_max > FP_L_SMEM) {         // factor scratch: one slot per SM (one CTA per SM at these degrees)
-        const size_t fb = (size_t)c->num_sms * fp_solver_fac_bytes(3, L_max);
+    // global factor scratch (five stages, or degrees above FP_L_SMEM): one slot per CTA of the solve launch
+    if (const size_t fb = fp_solver_fac_scratch_bytes(tol->stages, L_max, c->num_sms)) {
         if (cudaMalloc((void**)&c->d_fac, fb) != cudaSuccess) { fp_destroy(c); return fail(FP_ENOMEM, "fp_setup: factor scratch"); }
     }
+    if (cudaMalloc((void**)&c->d_queue, sizeof(int)) != cudaSuccess) { fp_destroy(c); return fail(FP_ENOMEM, "fp_setup: work counter"); }
     // block structure of every degree 2..L_max, packed into one device buffer
     {
         std::vector<FpBlkHost> bl(L_max + 1);
@@ -229,8 +231,12 @@ int fp_solve_batch(fp_ctx* ctx, const fp_instance* d_inst, int n, double* d_m, d
     cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     if ((int)sm > max_sm)
         return fail(FP_EUNSUPPORTED, "fp_solve_batch: %zu bytes of shared memory needed, %d available", sm, max_sm);
+    // CTAs take instances from the context's work counter, so one that finishes
+    // early takes the next (per-instance cost varies with the voxel's field)
+    if (cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+        return fail(FP_ECUDA, "fp_solve_batch: work counter reset failed");
     int rc = fp_launch_solve(ctx->tol.stages, &tab, &ctx->blk, &ctx->mat, &ctx->drv, &ctx->tol, d_inst, n, ctx->L_max,
-                             d_m, d_dmdt, d_status, d_stats, ctx->num_sms, (cudaStream_t)stream, nullptr, nullptr,
+                             d_m, d_dmdt, d_status, d_stats, ctx->num_sms, (cudaStream_t)stream, nullptr, ctx->d_queue,
                              ctx->d_fac);
     if (rc != FP_OK) return fail(rc, "fp_solve_batch: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return FP_OK;

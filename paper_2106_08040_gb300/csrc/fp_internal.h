@@ -162,7 +162,10 @@ void fp_gauss_legendre(int n, double* x, double* w);
 #include <cuda_runtime.h>
 size_t fp_solver_smem_bytes(int stages, int L);
 size_t fp_solver_fac_bytes(int stages, int L);     // global factor bytes per CTA (0 when they fit in shared memory)
-// d_fac: factor scratch of at least num_sms * fp_solver_fac_bytes(stages, L_launch) bytes when that is nonzero
+int fp_solver_ctas_per_sm(int stages, int L);     // CTAs per SM of the solve launch (one factor slot each)
+// bytes of the factor scratch a solve launch at (stages, L) needs on num_sms SMs (0: none)
+size_t fp_solver_fac_scratch_bytes(int stages, int L, int num_sms);
+// d_fac: factor scratch of at least fp_solver_fac_scratch_bytes(stages, L_launch, num_sms) bytes when that is nonzero
 int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
                     const fp_tol* tol, const fp_instance* d_inst, int n, int L_launch, double* d_m, double* d_dmdt,
                     int* d_status, int* d_stats, int num_sms, cudaStream_t st, const int* d_order, int* d_queue,
@@ -192,7 +195,8 @@ struct fp_ctx {
     DevBlk blk;               // device block structure, all degrees 2..L_max
     void* d_blk_mem;          // one allocation backing blk
     double* d_tw;             // twiddles cos/sin(2 pi q / S_p), q < S_p (fp_signal)
-    unsigned char* d_fac;     // factor scratch for L_max > FP_L_SMEM (num_sms CTAs), else NULL
+    unsigned char* d_fac;     // factor scratch of the solve launch (five stages or L_max > FP_L_SMEM), else NULL
+    int* d_queue;             // work counter of fp_solve_batch (instances taken one at a time by the CTAs)
 };
 
 int fp_fail(int code, const char* fmt, ...);

@@ -91,7 +91,7 @@ struct Layout {
     int N, L, nmax;
     size_t y, Z, F, f0, yb, diag, rr, zr, rc, zc, dnv, upv, fr, fc, Xr, Xc, lam, aw, ic, total;
     size_t fsum;
-    bool gfac;              // factors in global memory (degree above FP_L_SMEM); fr, fc are then offsets into it
+    bool gfac;              // factors in global memory (five stages, or degree above FP_L_SMEM); fr, fc are then offsets into it
     size_t fac_bytes;       // bytes of the factors of one instance
 };
 
@@ -120,7 +120,10 @@ __host__ __device__ inline Layout make_layout(int L) {
     ly.zc = o;   o = al16(o + (size_t)NC * N * 8);
     ly.dnv = o;  o = al16(o + N * FP_NLT * 4);
     ly.upv = o;  o = al16(o + N * FP_NLT * 4);
-    ly.gfac = L > FP_L_SMEM;
+    // five-stage factors (132 KB at degree 16) live in a global, L2-resident
+    // slot per CTA so that two CTAs share an SM; three-stage factors stay in
+    // shared memory up to degree FP_L_SMEM
+    ly.gfac = L > FP_L_SMEM || (S == 5 && !ADJ);
     ly.fac_bytes = al16(fsum * 4) + al16((size_t)NC * fsum * 8);
     if (ly.gfac) {
         ly.fr = 0;
@@ -151,6 +154,10 @@ size_t fp_solver_smem_bytes(int stages, int L) {
 size_t fp_solver_fac_bytes(int stages, int L) {
     const Layout ly = stages == 5 ? make_layout<5>(L) : make_layout<3>(L);
     return ly.gfac ? ly.fac_bytes : 0;
+}
+int fp_solver_ctas_per_sm(int stages, int L) { return stages == 5 && L <= FP_L_SMEM ? 2 : 1; }
+size_t fp_solver_fac_scratch_bytes(int stages, int L, int num_sms) {
+    return (size_t)num_sms * fp_solver_ctas_per_sm(stages, L) * fp_solver_fac_bytes(stages, L);
 }
 size_t fp_adjoint_smem_bytes(int stages, int L) {
     return stages == 5 ? make_layout<5, true>(L).total : make_layout<3, true>(L).total;
@@ -1091,7 +1098,8 @@ __device__ FwdOut forward_instance(Ctx<S>& C, const KArgs& A, int inst, const Fp
 }
 
 template <int S, int RS>
-__global__ void __launch_bounds__(NT, 1) fp_solve_kernel(KArgs A) {
+// five stages: 128 registers a thread, two CTAs per SM (factors in global memory)
+__global__ void __launch_bounds__(NT, S == 5 ? 2 : 1) fp_solve_kernel(KArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared<S> sh;
     Ctx<S> C;
@@ -1699,10 +1707,20 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
         return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
     }
     if (stages == 5) {
+        // one global factor slot per CTA, up to two CTAs per SM
+        if (!d_fac) return FP_EUNSUPPORTED;
+        A.fac = d_fac;
+        A.fac_stride = fp_solver_fac_bytes(5, L_launch);
         const size_t sm = fp_solver_smem_bytes(5, L_launch);
         e = cudaFuncSetAttribute(fp_solve_kernel<5, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return FP_ECUDA;
-        const int grid = n < num_sms ? n : num_sms;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp_solve_kernel<5, 1>, NT, sm) != cudaSuccess)
+            per_sm = 1;
+        const int slots = fp_solver_ctas_per_sm(5, L_launch);
+        per_sm = per_sm < 1 ? 1 : (per_sm > slots ? slots : per_sm);
+        const int cap = per_sm * num_sms;
+        const int grid = n < cap ? n : cap;
         fp_solve_kernel<5, 1><<<grid, NT, sm, st>>>(A);
         return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ECUDA;
     }

@@ -32,7 +32,7 @@ struct FpBucket {
     int stages;
     int refactor_every;
     float tuned_ms;   // autotune time of the chosen candidate (0 if not tuned)
-    unsigned char* d_fac;   // factor scratch of this bucket (degrees above FP_L_SMEM), else NULL
+    unsigned char* d_fac;   // factor scratch of this bucket (five stages or degrees above FP_L_SMEM), else NULL
 };
 
 struct fp_sweep {
@@ -180,12 +180,18 @@ int fp_sweep_plan(fp_ctx* ctx, const fp_instance* h_inst, int n, int bucket_widt
                                  0.f, nullptr});
     const int nb = (int)sw->b.size();
     int rc = FP_OK;
-    // buckets above FP_L_SMEM keep their factors in global memory: one scratch
-    // per bucket (buckets run concurrently on side streams), one slot per SM
-    for (auto& bk : sw->b)
-        if (rc == FP_OK && bk.L > FP_L_SMEM &&
-            cudaMalloc((void**)&bk.d_fac, (size_t)ctx->num_sms * fp_solver_fac_bytes(3, bk.L)) != cudaSuccess)
+    // five-stage buckets and buckets above FP_L_SMEM keep their factors in global
+    // memory: one scratch per bucket (buckets run concurrently on side streams),
+    // one slot per CTA, sized for either stage count the autotuner may pick
+    for (auto& bk : sw->b) {
+        size_t fb = fp_solver_fac_scratch_bytes(3, bk.L, ctx->num_sms);
+        if (bk.L <= FP_L_SMEM) {
+            const size_t f5 = fp_solver_fac_scratch_bytes(5, bk.L, ctx->num_sms);
+            fb = f5 > fb ? f5 : fb;
+        }
+        if (rc == FP_OK && fb && cudaMalloc((void**)&bk.d_fac, fb) != cudaSuccess)
             rc = fp_fail(FP_ENOMEM, "fp_sweep_plan: factor scratch at L=%d", bk.L);
+    }
     if (cudaMalloc(&sw->d_order, sizeof(int) * n) != cudaSuccess || cudaMalloc(&sw->d_tune, sizeof(int) * n) != cudaSuccess ||
         cudaMalloc(&sw->d_queue, sizeof(int) * nb) != cudaSuccess)
         rc = fp_fail(FP_ENOMEM, "fp_sweep_plan: cudaMalloc");
