@@ -484,6 +484,9 @@ def models_leg(fp, dev, peak64, Q=96, J2=96):
     return out
 
 
+STATUS_NAMES = {1: "MAXSTEPS", 2: "STEP_UNDERFLOW", 3: "NONFINITE", 4: "NEWTON_FAIL", 5: "BAD_INPUT", 6: "UNRESOLVED"}
+
+
 def sweep_leg(fp, dev, n_inst):
     """Uneven sweep: draws of the uneven-sweep distribution (64 x 64 voxel
     offsets, 16 Fibonacci axes, K log-uniform, d log-normal) with L per
@@ -524,9 +527,12 @@ def sweep_leg(fp, dev, n_inst):
     per_L = {}
     for Lv in np.unique(draw["L"]):
         sel = draw["L"] == Lv
+        codes = np.bincount(status[sel], minlength=7)
         per_L[int(Lv)] = {"instances": int(sel.sum()), "ok": int((status[sel] == 0).sum()),
                           "unresolved": int((status[sel] == 6).sum()),
-                          "other": int(((status[sel] != 0) & (status[sel] != 6)).sum())}
+                          "other": int(((status[sel] != 0) & (status[sel] != 6)).sum()),
+                          "other_by_status": {STATUS_NAMES.get(c, str(c)): int(codes[c])
+                                              for c in range(len(codes)) if c not in (0, 6) and codes[c]}}
     out = {"instances": n, "per_degree": per_L,
            "ms": ms, "instance_periods_per_s": n * periods / (ms * 1e-3), "status_ok": int((status == 0).sum()),
            "status_unresolved": int((status == 6).sum()), "autotune_s": t_tune, "buckets": sw.info(),
