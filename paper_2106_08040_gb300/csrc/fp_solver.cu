@@ -1,10 +1,12 @@
 // Batched Fokker-Planck solver for Neel rotation (Sec. 2.1, Eq. FP-general,
 // Eq. convection, Eq. mean_magmom_FP) on sm_103a.
 //
-// One CTA owns one instance at a time (persistent loop over instances).  The
-// real-SH coefficient vector c (N = (L+1)^2 doubles), every Radau stage and
-// the FP32 factors live in shared memory; nothing is streamed from HBM per
-// step except the L1/L2-resident coupling tables shared by all instances.
+// One CTA owns one instance at a time (persistent loop over instances, taken
+// from a work counter).  The real-SH coefficient vector c (N = (L+1)^2
+// doubles) and every Radau stage live in shared memory; the FP32 factors too
+// with 3 stages up to degree FP_L_SMEM, otherwise in a global slot per CTA
+// that stays in L2 (5 stages: two CTAs per SM).  Nothing is streamed from HBM
+// per step except the L1/L2-resident coupling tables shared by all instances.
 //
 // Time step: S-stage Radau IIA (S = 3: order 5, S = 5: order 9; L-stable),
 // simplified Newton:
@@ -13,8 +15,9 @@
 // Abar = A(t_f + h_f) is frozen over several steps.  Lam - h_f Abar splits into
 // one real and (S-1)/2 complex systems, each block-tridiagonal in |m|; every
 // system is factorised (block Thomas) into explicit FP32 inverses of its
-// Schur-complement diagonal blocks, one warp per system (Gauss-Jordan with
-// partial pivoting in registers), and solved by one warp per system.
+// Schur-complement diagonal blocks by a group of warps per system
+// (Gauss-Jordan with partial pivoting in registers, one named barrier per
+// pivot) and solved by the same group.
 // Embedded error estimate filtered through the real factor; steps land on
 // every output sample time.
 #include <cuda_runtime.h>
