@@ -78,10 +78,10 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15
 // are reused while h / h_factor stays in [FP_HRAT_LO, FP_HRAT_HI] and are
 // refreshed after a step whose contraction rate exceeded FP_THETA_REFAC.
 #ifndef FP_KAPPA
-#define FP_KAPPA 0.1f
+#define FP_KAPPA 0.2f
 #endif
 #ifndef FP_THETA_REFAC
-#define FP_THETA_REFAC 0.1f
+#define FP_THETA_REFAC 0.05f
 #endif
 #ifndef FP_HRAT_LO
 #define FP_HRAT_LO 0.8
