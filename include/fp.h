@@ -235,11 +235,11 @@ long long fp_grad_workspace_bytes(const fp_ctx* ctx, int n);
  * replay, 3 transposed stage solve) and the step index where it failed (-1 if
  * none).  Gradients of instances whose status is not FP_STATUS_OK are 0.
  * d_work: device workspace of
- * work_bytes >= fp_grad_workspace_bytes(ctx, n), owned by the caller, contents
- * undefined on return.  Asynchronous on `stream`.  The adjoint keeps one more
- * state and stage block in shared memory than the solve: with 5 stages at
- * L_max = 16 that exceeds the 227 KB per CTA and the call returns
- * FP_EUNSUPPORTED (use a 3-stage context for gradients at that degree). */
+ * work_bytes >= fp_grad_workspace_bytes(ctx, n), 16-byte aligned (FP_EINVAL
+ * otherwise; cudaMalloc gives 256), owned by the caller, contents undefined on
+ * return.  With 5 stages each CTA's share of it opens with that CTA's FP32
+ * factors (131 KB at L_max = 16), the rest of the adjoint state sits in shared
+ * memory.  Asynchronous on `stream`. */
 int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max,
             const double* h_channels, int C, const double* d_dJ_dphihat,
             double* d_grad, int* d_status, int* d_stats, void* d_work,

@@ -257,6 +257,8 @@ int fp_grad(fp_ctx* ctx, const fp_instance* d_inst, int n, int k_max, const doub
     if (n == 0) return FP_OK;
     if (!d_inst || !d_dJ_dphihat || !d_grad || !d_status || !h_channels || !d_work)
         return fail(FP_EINVAL, "fp_grad: NULL buffer");
+    if ((reinterpret_cast<unsigned long long>(d_work) & 15ull) != 0)
+        return fail(FP_EINVAL, "fp_grad: workspace not 16-byte aligned");
     if (ctx->L_max > FP_L_SMEM)
         return fail(FP_EUNSUPPORTED, "fp_grad: the adjoint supports L_max <= %d (context has %d)", FP_L_SMEM, ctx->L_max);
     if (k_max < 0 || k_max >= ctx->drv.samples_per_period) return fail(FP_EINVAL, "fp_grad: k_max=%d", k_max);

@@ -123,10 +123,11 @@ __host__ __device__ inline Layout make_layout(int L) {
     ly.zc = o;   o = al16(o + (size_t)NC * N * 8);
     ly.dnv = o;  o = al16(o + N * FP_NLT * 4);
     ly.upv = o;  o = al16(o + N * FP_NLT * 4);
-    // five-stage factors (132 KB at degree 16) live in a global, L2-resident
-    // slot per CTA so that two CTAs share an SM; three-stage factors stay in
-    // shared memory up to degree FP_L_SMEM
-    ly.gfac = L > FP_L_SMEM || (S == 5 && !ADJ);
+    // five-stage factors (131 KB at degree 16) live in a global, L2-resident
+    // slot per CTA (the solve: two CTAs per SM; the adjoint: the slot opens
+    // its workspace); three-stage factors stay in shared memory up to degree
+    // FP_L_SMEM
+    ly.gfac = L > FP_L_SMEM || S == 5;
     ly.fac_bytes = al16(fsum * 4) + al16((size_t)NC * fsum * 8);
     if (ly.gfac) {
         ly.fr = 0;
@@ -164,6 +165,12 @@ size_t fp_solver_fac_scratch_bytes(int stages, int L, int num_sms) {
 }
 size_t fp_adjoint_smem_bytes(int stages, int L) {
     return stages == 5 ? make_layout<5, true>(L).total : make_layout<3, true>(L).total;
+}
+// global factor doubles at the head of each adjoint CTA's workspace (0 when the
+// factors fit in shared memory), even so that every CTA's slot is 16-byte aligned
+static size_t adjoint_fac_doubles(int stages, int L) {
+    const Layout ly = stages == 5 ? make_layout<5, true>(L) : make_layout<3, true>(L);
+    return ly.gfac ? ((ly.fac_bytes + 15) / 16) * 2 : 0;
 }
 
 // --------------------------------------------------- scalar/complex ops ----
@@ -1432,6 +1439,7 @@ struct GArgs {
     int C, K;
     double* work;           // per CTA: work_per_cta doubles
     size_t work_per_cta;
+    size_t fac_doubles;     // global factors at the head of each CTA's workspace (0: in shared memory)
     int max_rec;
 };
 
@@ -1443,11 +1451,11 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
     const KArgs& A = G.A;
     const DevTab& T = A.tab;
     Ctx<S> C;
-    bind_smem<S, true>(C, smem, A.L_launch, sh, nullptr);
     const int Sp = A.drv.samples_per_period, j0 = A.S_out - Sp;
     const int Nmax = (A.L_launch + 1) * (A.L_launch + 1);
-    double* ws = G.work + (size_t)blockIdx.x * G.work_per_cta;
-    double* ws_steps = ws;                                              // [max_rec][FP_REC]
+    double* ws = G.work + (size_t)blockIdx.x * G.work_per_cta;          // [fac_doubles] factors (5 stages)
+    bind_smem<S, true>(C, smem, A.L_launch, sh, G.fac_doubles ? (unsigned char*)ws : nullptr);
+    double* ws_steps = ws + G.fac_doubles;                              // [max_rec][FP_REC]
     double* ws_ckpt = ws_steps + (size_t)G.max_rec * FP_REC;            // [max_rec/CKPT + 1][Nmax]
     double* ws_seg = ws_ckpt + (size_t)(G.max_rec / FP_CKPT + 1) * Nmax; // [CKPT + 1][Nmax]
     double* ws_g = ws_seg + (size_t)(FP_CKPT + 1) * Nmax;                // [Sp][3]
@@ -1746,8 +1754,10 @@ int fp_launch_solve(int stages, const DevTab* tab, const DevBlk* blk, const fp_m
 
 size_t fp_adjoint_work_doubles_per_cta(int stages, int L_max, int S_p, int max_rec) {
     const size_t Nmax = (size_t)(L_max + 1) * (L_max + 1);
-    return (size_t)max_rec * FP_REC + (size_t)(max_rec / FP_CKPT + 1) * Nmax + (size_t)(FP_CKPT + 1) * Nmax +
-           (size_t)S_p * 3 + (size_t)FP_CKPT * stages * Nmax;
+    const size_t d = adjoint_fac_doubles(stages, L_max) + (size_t)max_rec * FP_REC +
+                     (size_t)(max_rec / FP_CKPT + 1) * Nmax + (size_t)(FP_CKPT + 1) * Nmax + (size_t)S_p * 3 +
+                     (size_t)FP_CKPT * stages * Nmax;
+    return (d + 1) & ~(size_t)1;                      // even: CTA slots stay 16-byte aligned
 }
 
 int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp_material* mat, const fp_drive* drv,
@@ -1781,6 +1791,7 @@ int fp_launch_adjoint(int stages, const DevTab* tab, const DevBlk* blk, const fp
     G.work = d_work;
     G.max_rec = max_rec;
     G.work_per_cta = fp_adjoint_work_doubles_per_cta(stages, L_launch, drv->samples_per_period, max_rec);
+    G.fac_doubles = adjoint_fac_doubles(stages, L_launch);
     size_t sm = fp_adjoint_smem_bytes(stages, L_launch);
     cudaError_t e;
     if (stages == 5) {

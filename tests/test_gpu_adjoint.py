@@ -129,21 +129,23 @@ def test_autograd_function_matches_fp_grad(fp):
     np.testing.assert_allclose(params.grad.cpu().numpy(), g_ref, rtol=1e-9, atol=0)
 
 
-def test_adjoint_L16_lissajous_vs_gpu_central_differences(fp):
+@pytest.mark.parametrize("stages", [3, 5])
+def test_adjoint_L16_lissajous_vs_gpu_central_differences(fp, stages):
     """Where the gradients are used: system-matrix voxels 0 and 1 (L = 16,
     cosine Lissajous drive, 1 warm-up + 1 output period, 1632 samples, all 817
     harmonics of both channels in J).  Both have transposed stage solves that
     stagnate near the single-precision level of the factor solves.  The
-    adjoint (3 stages, rtol 1e-10) against central differences (relative step
-    1e-4) of the 5-stage forward at rtol 1e-11: within 1e-5 of the gradient
-    norm per parameter."""
+    adjoint (3 or 5 stages, rtol 1e-10; with 5 stages its factors live in the
+    workspace) against central differences (relative step 1e-4) of the 5-stage
+    forward at rtol 1e-11: within 1e-5 of the gradient norm per parameter."""
     dspec, inst = workloads.system_matrix_workload()
     inst = inst[:2]
     n, K = len(inst), 816
     ch = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     G = np.random.default_rng(3).normal(size=(n, 2, K + 1, 2))
     dev = torch.device("cuda")
-    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-10, stages=3, max_steps=400000), 16)
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__),
+                     fp.Tol(rtol=1e-10, stages=stages, max_steps=400000), 16)
     grad = torch.empty((n, 4), dtype=torch.float64, device=dev)
     st = torch.empty((n,), dtype=torch.int32, device=dev)
     stats = torch.empty((n, 4), dtype=torch.int32, device=dev)
