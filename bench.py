@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the uneven-sweep measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    p.add_argument("--adjoint-stages", type=int, default=3, choices=(3, 5), help="Radau stages of the adjoint leg")
     p.add_argument("--no-models", action="store_true", help="skip the M0/M1/M2 model measurement")
     p.add_argument("--m1-dictionary", type=int, default=96, help="M1 fit: dictionary elements per call")
     p.add_argument("--m2-tuples", type=int, default=96, help="M2: (D, K) tuples in the dictionary")
@@ -318,7 +319,7 @@ def surrogate_leg(fp, dev):
             "error_reference": "fp_solve_batch + fp_signal, L = 16, rtol 1e-7, 152 fresh draws of the training domain"}
 
 
-def adjoint_leg(fp, dev, n_inst=152):
+def adjoint_leg(fp, dev, n_inst=152, stages=3):
     """Discrete adjoint (fp_grad) on the first voxels of the system-matrix batch:
     gradients dJ/d(K, d, theta, phi) of a seeded linear functional of phi_hat,
     timed against the forward solve + phi_hat of the same instances."""
@@ -326,7 +327,7 @@ def adjoint_leg(fp, dev, n_inst=152):
     from paper_2106_08040_gb300 import workloads
     dspec, inst = workloads.system_matrix_workload()
     inst = inst[:n_inst]
-    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=3, max_steps=200000), 16)
+    ctx = fp.Context(fp.Material(), fp.Drive(**dspec.__dict__), fp.Tol(rtol=1e-9, stages=stages, max_steps=200000), 16)
     n, K = len(inst), 816
     ch = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     d_inst = fp.instances_to_device(inst, dev)
@@ -375,7 +376,7 @@ def adjoint_leg(fp, dev, n_inst=152):
         w = np.array([inst[i]["K"], inst[i]["d"], 1.0, 1.0])
         rel_err.append((np.abs((g[i] - fd) * w) / np.linalg.norm(fd * w)).tolist())
     ctx5.close()
-    out = {"instances": n, "forward_ms": t_f, "adjoint_ms": t_a, "adjoint_over_forward": t_a / t_f,
+    out = {"instances": n, "radau_stages": stages, "forward_ms": t_f, "adjoint_ms": t_a, "adjoint_over_forward": t_a / t_f,
            "gradients_per_s": n / (t_a * 1e-3), "instance_periods_per_s": n * periods / (t_a * 1e-3),
            "adjoint_fit_iteration_s_extrapolated": 64 * 1024 / (n / (t_a * 1e-3)),
            "adjoint_fit_iteration_note": "64 candidate sets x 32 x 32 voxels = 65,536 gradient evaluations of this "
@@ -388,8 +389,8 @@ def adjoint_leg(fp, dev, n_inst=152):
                                                    "reference": "central differences, relative step 1e-4, of "
                                                                 "fp_solve_batch + fp_signal at rtol 1e-11 (5 stages); "
                                                                 "error in units of the gradient norm"},
-           "workload": "first %d voxels of the 32x32 system-matrix batch, L = 16, Radau s = 3, rtol 1e-9, "
-                       "checkpoints every 64 steps" % n}
+           "workload": "first %d voxels of the 32x32 system-matrix batch, L = 16, Radau s = %d, rtol 1e-9, "
+                       "checkpoints every 64 steps" % (n, stages)}
     ctx.close()
     return out
 
@@ -672,7 +673,7 @@ def run_gpu(args):
         if not args.no_sweep:
             out["sweep"] = sweep_leg(fp, dev, args.sweep_instances)
         if not args.no_adjoint:
-            out["adjoint"] = adjoint_leg(fp, dev)
+            out["adjoint"] = adjoint_leg(fp, dev, stages=args.adjoint_stages)
         if not args.no_models:
             out["models"] = models_leg(fp, dev, peak / 1e3, args.m1_dictionary, args.m2_tuples)
     if world > 1:

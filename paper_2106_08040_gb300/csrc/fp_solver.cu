@@ -1520,6 +1520,7 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
             // forward's own iteration error of the recorded path
             sc_rep = A.tol.atol + A.tol.rtol * (double)block_max(ym, sh.red);
             fac_valid = false;                     // the last factors belong to a later time
+            double h_prev = 0.0;                   // the previous replayed step (its stages are in Z)
             for (int n = n0; n < n1; ++n) {
                 const double* rs = ws_steps + (size_t)n * FP_REC;
                 const double t = rs[0], hs = rs[1];
@@ -1527,8 +1528,11 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
                     refactor<S>(C, A, P, R, off, rs[3], rs[4], sh);
                     t_fc = rs[3]; h_f = rs[4]; fac_valid = true;
                 }
-                stage_scalars<S>(A, P, R, off, t, hs, false, 1.0, sh);
-                predict_stages<S>(C, false, sh);
+                // start from the previous step's collocation polynomial, as the
+                // forward pass did (accepted steps are contiguous)
+                const bool pred = h_prev > 0.0;
+                stage_scalars<S>(A, P, R, off, t, hs, pred, pred ? h_prev : 1.0, sh);
+                predict_stages<S>(C, pred, sh);
                 float eta = 1.f;
                 NewtonResult nr = newton_stages<S>(C, T, hs, h_f, sc_rep, eta, 0.02f, 4 * A.tol.newton_max_iter, sh);
                 // a stalled iteration whose last increment is already below the
@@ -1548,6 +1552,7 @@ __global__ void __launch_bounds__(NT, 1) fp_adjoint_kernel(GArgs G) {
                     fail_phase = 2; fail_step = n;
                     break;
                 }
+                h_prev = hs;
                 double* zs = ws_Z + (size_t)(n - n0) * S * N;
                 for (int e = threadIdx.x; e < S * N; e += NT) zs[e] = C.Z[e];
                 for (int i = threadIdx.x; i < N; i += NT) {
