@@ -411,7 +411,9 @@ int fp_m2_gram(const double* d_phi, const double* d_a, const double* d_S, const 
  * complex rows split into real and imaginary parts; s = s_rank (<= 0: all
  * numerically nonzero singular values).  The quadratic program
  * min 1/2 w^T Q w + f^T w, w >= 0 is solved by a primal-dual interior-point
- * method.  Outputs: h_w [J], *h_objective = the truncated objective,
+ * method; the weight of a column that is zero in the truncated problem (it
+ * cannot change the objective) is set to 0, as are all weights at rank 0.
+ * Outputs: h_w [J], *h_objective = the truncated objective,
  * *h_residual = ||M w - y||_2^2, h_sv [J] = singular values of M (each of
  * the three may be NULL).  Returns the rank s used (>= 0), or a negative
  * FP_E* code (FP_EUNSUPPORTED if the iteration does not converge).  The

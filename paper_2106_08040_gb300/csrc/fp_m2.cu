@@ -237,17 +237,22 @@ static double qp_value(int n, const std::vector<double>& Q, const std::vector<do
 }
 
 // Polish an interior-point solution: the components with w_i > z_i are taken
-// as free, the rest as zero, and the free block solves Q_FF w_F = -f_F.  The
-// result is kept if it is non-negative and does not raise the objective
-// (interior points approach a degenerate optimum, where the gradient vanishes
-// on zero weights too, only like sqrt(mu)).
+// as free, the rest as zero, and the free block solves Q_FF w_F = -f_F (no
+// free component: the candidate is w = 0).  The result is kept if it is
+// non-negative and does not raise the objective (interior points approach a
+// degenerate optimum, where the gradient vanishes on zero weights too, only
+// like sqrt(mu)).
 static void qp_polish(int n, const std::vector<double>& Q, const std::vector<double>& f, std::vector<double>& w,
                       const std::vector<double>& z) {
     std::vector<int> F;
     for (int i = 0; i < n; ++i)
         if (w[i] > z[i]) F.push_back(i);
     const int m = (int)F.size();
-    if (m == 0) return;
+    if (m == 0) {
+        const std::vector<double> w0(n, 0.0);
+        if (qp_value(n, Q, f, w0) <= qp_value(n, Q, f, w)) w = w0;
+        return;
+    }
     std::vector<double> K((size_t)m * m), x(m);
     for (int a = 0; a < m; ++a) {
         x[a] = -f[F[a]];
@@ -378,8 +383,27 @@ int fp_m2_solve(const double* h_G, int J, int s_rank, double* h_w, double* h_obj
             f[i] -= gi * hr[r];
             for (int j = 0; j < J; ++j) Q[(size_t)i * J + j] += gi * Gr[(size_t)r * J + j];
         }
-    const int its = qp_nonneg(J, Q, f, w);
-    if (its < 0) return fp_fail(FP_EUNSUPPORTED, "fp_m2_solve: interior-point iteration did not converge (%d)", its);
+    // weights of dictionary columns that are zero in the truncated problem
+    // (Q_ii = |column i|^2 = 0, hence f_i = 0) leave the objective unchanged:
+    // they are set to 0 and the QP runs over the others
+    double qmax = 0.0;
+    for (int i = 0; i < J; ++i) qmax = std::max(qmax, Q[(size_t)i * J + i]);
+    std::vector<int> act;
+    for (int i = 0; i < J; ++i)
+        if (Q[(size_t)i * J + i] > 1e-24 * qmax) act.push_back(i);
+    const int na = (int)act.size();
+    w.assign(J, 0.0);
+    if (na > 0) {
+        std::vector<double> Qa((size_t)na * na), fa(na), wa;
+        for (int a = 0; a < na; ++a) {
+            fa[a] = f[act[a]];
+            for (int b = 0; b < na; ++b) Qa[(size_t)a * na + b] = Q[(size_t)act[a] * J + act[b]];
+        }
+        const int its = qp_nonneg(na, Qa, fa, wa);
+        if (its < 0)
+            return fp_fail(FP_EUNSUPPORTED, "fp_m2_solve: interior-point iteration did not converge (%d)", its);
+        for (int a = 0; a < na; ++a) w[act[a]] = wa[a];
+    }
     double obj = 0.0;                                    // ||Gr w - hr||^2
     for (int r = 0; r < 2 * s; ++r) {
         double v = -hr[r];

@@ -75,3 +75,28 @@ def test_m2_solve_matches_oracle(fp, s_rank):
         assert s == 4
         assert abs(obj - objo) <= 1e-9 * objo
         assert abs(np.sqrt(res) - np.linalg.norm(M @ w - y)) <= 1e-9 * np.linalg.norm(y)
+
+
+def test_m2_solve_degenerate_problems(fp):
+    """Degenerate M2 problems with a unique answer: zero data gives zero
+    weights; data in the negative cone of the dictionary gives zero weights; a
+    dictionary column that is identically zero gets weight 0 while the others
+    equal a library NNLS solve of the real-split least-squares problem; an
+    all-zero dictionary has rank 0 and zero weights."""
+    scipy_optimize = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(11)
+    M = _rand_complex(rng, (50, 4))
+    w, obj, res, sv, s = fp.fp_m2_solve(_gram(M, np.zeros(50, complex)), 4)
+    assert s == 4 and (w == 0).all() and res == 0.0
+    w, _, _, _, _ = fp.fp_m2_solve(_gram(M, -(M @ np.array([1.0, 0.5, 0.2, 0.3]))), 4)
+    assert (w == 0).all()
+    y = M @ np.array([1.0, 0.5, 0.2, 0.3]) + 0.1 * _rand_complex(rng, 50)
+    Mz = M.copy()
+    Mz[:, 2] = 0.0
+    w, obj, res, sv, s = fp.fp_m2_solve(_gram(Mz, y), 4)
+    ref, rnorm = scipy_optimize.nnls(np.concatenate([Mz.real, Mz.imag]), np.concatenate([y.real, y.imag]))
+    assert s == 3 and w[2] == 0.0 and sv[3] == 0.0
+    np.testing.assert_allclose(w, ref, rtol=1e-9, atol=1e-12)
+    assert abs(res - rnorm ** 2) <= 1e-9 * rnorm ** 2
+    w, obj, res, sv, s = fp.fp_m2_solve(_gram(np.zeros((10, 3), complex), np.zeros(10, complex)), 3)
+    assert s == 0 and (w == 0).all() and (sv == 0).all()
