@@ -53,3 +53,24 @@ def test_closed_form_tables_match_oracle_weak_form(fp, L):
 def test_bad_arguments_return_errors(fp):
     with pytest.raises(RuntimeError, match="L=1"):
         fp.fp_operator_dense(fp.Material(), 1, 1e3, 2e-8, [0, 0, 0])
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libfp.so the binding raises at the first call; there is no
+    fallback path (checked in a child process so the loaded library of this
+    session is untouched)."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2106_08040_gb300 import _lib, fp\n"
+        "_lib.LIB_PATH = %r\n"
+        "try:\n"
+        "    fp.fp_max_degree()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e); sys.exit(0)\n"
+        "sys.exit(3)\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), str(tmp_path / "libfp.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "not built" in r.stdout
